@@ -1,0 +1,515 @@
+"""Benchmark: batched stable closed-form 3x3 eigenvalues on GB300.
+
+One step = one forward + backward pass of the whole path over the mixed
+workload of 2^28 matrices per GPU: 2^27 symmetric 6-entry binary32 matrices
+through the compensated binary32 kernels and 2^27 general 9-entry binary64
+matrices through the binary64 kernels (invariants I1, J2, J3, Delta ->
+triple angle -> eigenvalues -> adjoint), replayed from one CUDA graph.
+Inputs are resident in HBM and larger than L2 (about 18 GB per step), so no
+L2 flush is needed between steps.
+
+Printed (rank 0, one JSON line): whole-job throughput in G matrices/s, the
+roofline of the dominant kernel (binary64 general forward) measured live with
+CUDA events, per-path throughputs of the other workloads' shapes, the CPU
+oracle timed on the host cores on a bounded sample (with the max error over
+the stability bound of the GPU results on that sample), an end-to-end number
+through host buffers, and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G matrices/s fwd and fwd+bwd (FP64 vs FP32-comp) vs roofline; max err/stab bound"
+UNIT = "G matrices/s"
+N_MIXED = 1 << 28
+WORKLOAD = ("mixed fwd+bwd, 2^28 matrices/GPU: 2^27 symmetric 6-entry FP32 (compensated FP32 "
+            "path) + 2^27 general 9-entry FP64 (FP64 path), scales 10^U[-8,8], 30% "
+            "triple-perturbed, one CUDA graph per step")
+
+# Binary64 operations per matrix executed by the general 9-entry binary64
+# forward kernel (eigenvalues + adjoint inputs), counted by ncu
+# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on.sum / n).
+FWD_F64_GEN_DFMA = 128
+FWD_F64_GEN_DMUL = 46
+FWD_F64_GEN_DADD = 40
+FWD_F64_GEN_FLOP = 2 * FWD_F64_GEN_DFMA + FWD_F64_GEN_DMUL + FWD_F64_GEN_DADD
+# Peak binary64 rate from the unit counts: 152 SMs x 2 FP64 FMA lanes x 2 flop x clock.
+FP64_LANES_PER_SM = 2
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def timed(fn, steps, stream):
+    """Average milliseconds of fn() over `steps` runs, CUDA events on `stream`."""
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+# --------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle on the host cores
+# --------------------------------------------------------------------------
+
+def oracle_step(oracle, S64, G64, wS, wG, threads):
+    """One forward + backward of the oracle over (S64 symmetric, G64 general),
+    chunked over `threads` host threads (the C calls release the GIL).
+    Returns the eigenvalues of both halves."""
+    def chunks(n):
+        k = max(1, threads)
+        return [(n * i // k, n * (i + 1) // k) for i in range(k)]
+
+    lamS = np.empty((S64.shape[0], 3))
+    lamG = np.empty((G64.shape[0], 3))
+
+    def work(args):
+        X, w, layout, lo, hi, out = args
+        out[lo:hi] = oracle.eigvals(X[lo:hi], layout=layout)
+        oracle.eigvals_grad(X[lo:hi], w[lo:hi], layout=layout)
+
+    jobs = [(S64, wS, oracle.SYM6, lo, hi, lamS) for lo, hi in chunks(S64.shape[0])]
+    jobs += [(G64, wG, oracle.GENERAL9, lo, hi, lamG) for lo, hi in chunks(G64.shape[0])]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(work, jobs))
+    return lamS, lamG
+
+
+def oracle_sample(n_half, seed, device="cpu"):
+    import workloads as W
+    w5 = W.workload5(n=2 * n_half, device=device, seed=seed)
+    S, G = w5["sym6"], w5["general9"]
+    return (S.A.double().cpu().numpy(), G.A.cpu().numpy(), S.extra["w"].double().cpu().numpy(),
+            G.extra["w"].cpu().numpy())
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n_half = 1 << 21
+    S64, G64, wS, wG = oracle_sample(n_half, seed=4005)
+    for _ in range(args.warmup):
+        oracle_step(oracle, S64, G64, wS, wG, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(oracle, S64, G64, wS, wG, threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2 * n_half / dt / 1e9
+    sample = (f"{2 * n_half} matrices per step ({n_half} symmetric FP32-valued + {n_half} general "
+              f"FP64) of the mixed workload, eigenvalues + eigenvector-form gradient")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_matrices_per_step": 2 * n_half},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# Our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import paper_2511_00292_gb300 as eig3
+    from paper_2511_00292_gb300 import build as _b
+    import workloads as W
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _b.build()
+    eig3.load()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- the mixed workload (inputs resident in HBM) ----
+    w5 = W.workload5(n=N_MIXED, device=dev, seed=1005 + 7919 * rank)
+    S, G = w5["sym6"], w5["general9"]
+    nS, nG = S.n, G.n
+    lamS = torch.empty(nS, 3, dtype=torch.float32, device=dev)
+    auxS = torch.empty(nS, 4, dtype=torch.float32, device=dev)
+    gS = torch.empty_like(S.A)
+    lamG = torch.empty(nG, 3, dtype=torch.float64, device=dev)
+    auxG = torch.empty(nG, 4, dtype=torch.float64, device=dev)
+    gG = torch.empty_like(G.A)
+    wS, wG = S.extra["w"], G.extra["w"]
+    stats = eig3.Stats(dev)
+
+    def fwd_S():
+        eig3.eigvals(S.A, precision="f32c", return_aux=True, out=lamS, aux_out=auxS, stats=stats)
+
+    def bwd_S():
+        eig3.eigvals_backward(S.A, wS, aux=auxS, precision="f32c", out=gS)
+
+    def fwd_G():
+        eig3.eigvals(G.A, precision="f64", return_aux=True, out=lamG, aux_out=auxG, stats=stats)
+
+    def bwd_G():
+        eig3.eigvals_backward(G.A, wG, aux=auxG, precision="f64", out=gG)
+
+    def step():
+        fwd_S()
+        bwd_S()
+        fwd_G()
+        bwd_G()
+
+    launches_per_step = 4
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    stats.reset()
+
+    # ---- timed region: K graph replays ----
+    barrier()
+    with ClockSampler(local) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+    barrier()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N_MIXED / (ms * 1e-3) / 1e9
+
+    # ---- per-kernel durations (eager, same launches, events on the launch stream) ----
+    kern = {}
+    for name, fn in (("fwd_f32c_sym6", fwd_S), ("bwd_f32c_sym6", bwd_S),
+                     ("fwd_f64_general9", fwd_G), ("bwd_f64_general9", bwd_G)):
+        fn()
+        kern[name] = timed(fn, args.steps, stream)
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = torch.cuda.get_device_properties(dev).multi_processor_count * \
+        FP64_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    t_fwdG = kern["fwd_f64_general9"] * 1e-3
+    achieved = FWD_F64_GEN_FLOP * nG / t_fwdG / 1e12
+    roofline = {"kernel": "k_eigvals<general9, f64, aux, stats> (binary64 forward)",
+                "bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops,
+                "traffic": None,
+                "peak_source": f"FP64 pipe from unit counts and clock: SMs x {FP64_LANES_PER_SM} "
+                               f"FMA/clk x 2 flop x {sm_max:.0f} MHz",
+                "algorithmic_flop_per_matrix": FWD_F64_GEN_FLOP,
+                "hbm_gbs_same_kernel": (72 + 24 + 32) * nG / t_fwdG / 1e9,
+                "hbm_peak_gbs": pk.get("hbm_gbs"), "hbm_peak_source": pk_src,
+                "kernel_ms": kern}
+
+    # ---- the other workloads' paths (fwd, fwd+bwd, FP64 vs compensated FP32) ----
+    paths = {}
+    if not args.skip_paths:
+        paths = measure_paths(eig3, W, dev, stream, args.steps)
+
+    # ---- end to end through host buffers (pinned), public API ----
+    e2e = measure_e2e(eig3, S, G, dev, stream, args.steps)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32c", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "matrices_per_gpu": N_MIXED,
+                      "l2": "inputs ~18 GB/step > 129 MB L2, no flush needed",
+                      "graph": "one CUDA graph per step (4 kernels), replayed"},
+           "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
+           "clocks": clocks.summary(), "e2e": e2e, "paths": paths,
+           "stats": stats.read()}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) ----
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        out["cpu_baseline"], out["max_err_over_bound"] = cpu_baseline(
+            eig3, S, G, lamS, lamG, gS, gG)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def measure_paths(eig3, W, dev, stream, steps):
+    paths = {}
+    steps = max(steps, 3)
+    b2 = W.workload2(n=1 << 26, device=dev)
+    lam = torch.empty(b2.n, 3, dtype=torch.float64, device=dev)
+    t = timed(lambda: eig3.eigvals(b2.A, out=lam), steps, stream)
+    paths["fwd_f64_general9_2^26"] = {"G_matrices_per_s": b2.n / t / 1e6, "ms": t}
+    del b2, lam
+    b3 = W.workload3(n=1 << 27, device=dev)
+    l3 = torch.empty(b3.n, 3, dtype=torch.float32, device=dev)
+    tc = timed(lambda: eig3.eigvals(b3.A, precision="f32c", out=l3), steps, stream)
+    td = timed(lambda: eig3.eigvals(b3.A, precision="f64", out=l3), steps, stream)
+    paths["fwd_sym6_fp32_storage_2^27"] = {
+        "f32c_G_matrices_per_s": b3.n / tc / 1e6, "f64_G_matrices_per_s": b3.n / td / 1e6,
+        "f32c_speedup_over_f64": td / tc}
+    del b3, l3
+    b4 = W.workload4(n=1 << 24, device=dev)
+    lam4 = torch.empty(b4.n, 3, dtype=torch.float64, device=dev)
+    aux4 = torch.empty(b4.n, 4, dtype=torch.float64, device=dev)
+    g4 = torch.empty_like(b4.A)
+    w4 = b4.extra["w"]
+
+    def fb():
+        eig3.eigvals(b4.A, out=lam4, return_aux=True, aux_out=aux4)
+        eig3.eigvals_backward(b4.A, w4, aux=aux4, out=g4)
+
+    t4 = timed(fb, steps, stream)
+    paths["fwd_bwd_f64_general9_2^24"] = {"G_matrices_per_s": b4.n / t4 / 1e6, "ms": t4}
+    del b4, lam4, aux4, g4
+    torch.cuda.empty_cache()
+    return paths
+
+
+def measure_e2e(eig3, S, G, dev, stream, steps):
+    """Same step through host buffers: H2D of the inputs (matrices and loss
+    weights) from pinned memory, the four library calls, D2H of eigenvalues
+    and gradients, all inside the timed region."""
+    hS = S.A.cpu().pin_memory()
+    hG = G.A.cpu().pin_memory()
+    hwS = S.extra["w"].cpu().pin_memory()
+    hwG = G.extra["w"].cpu().pin_memory()
+    olS = torch.empty(S.n, 3, dtype=torch.float32).pin_memory()
+    olG = torch.empty(G.n, 3, dtype=torch.float64).pin_memory()
+    ogS = torch.empty_like(hS).pin_memory()
+    ogG = torch.empty_like(hG).pin_memory()
+    dS, dG = torch.empty_like(S.A), torch.empty_like(G.A)
+    dwS, dwG = torch.empty_like(S.extra["w"]), torch.empty_like(G.extra["w"])
+
+    def e2e_step():
+        dS.copy_(hS, non_blocking=True)
+        dwS.copy_(hwS, non_blocking=True)
+        dG.copy_(hG, non_blocking=True)
+        dwG.copy_(hwG, non_blocking=True)
+        lS, aS = eig3.eigvals(dS, precision="f32c", return_aux=True)
+        gS = eig3.eigvals_backward(dS, dwS, aux=aS, precision="f32c")
+        lG, aG = eig3.eigvals(dG, precision="f64", return_aux=True)
+        gG = eig3.eigvals_backward(dG, dwG, aux=aG, precision="f64")
+        olS.copy_(lS, non_blocking=True)
+        ogS.copy_(gS, non_blocking=True)
+        olG.copy_(lG, non_blocking=True)
+        ogG.copy_(gG, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    k = max(1, min(steps, 3))
+    ms = timed(e2e_step, k, stream)
+    h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
+    d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
+    del hS, hG, hwS, hwG, olS, olG, ogS, ogG, dS, dG, dwS, dwG
+    return {"value": (S.n + G.n) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k}
+
+
+def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of
+    the workload; the same sample gives the max error over the stability bound
+    of the GPU results."""
+    import oracle
+    import workloads as W
+    oracle.build()
+    threads = os.cpu_count() or 1
+    k = 1 << 23
+    iS = torch.as_tensor(W.sample_indices(S.n, k, seed=11), device=S.A.device)
+    iG = torch.as_tensor(W.sample_indices(G.n, k, seed=12), device=G.A.device)
+    S64 = S.A[iS].double().cpu().numpy()
+    G64 = G.A[iG].cpu().numpy()
+    wS = S.extra["w"][iS].double().cpu().numpy()
+    wG = G.extra["w"][iG].cpu().numpy()
+    t0 = time.perf_counter()
+    refS, refG = oracle_step(oracle, S64, G64, wS, wG, threads)
+    dt = time.perf_counter() - t0
+    value = (S64.shape[0] + G64.shape[0]) / dt / 1e9
+    # accuracy of the GPU results on this sample
+    refS = np.sort(refS, axis=1)
+    refG = np.sort(refG, axis=1)
+    bS = oracle.bounds(S64, 1.0, layout=oracle.SYM6, u=2.0 ** -24)[:, 4]
+    bG = oracle.bounds(G64, G.kappa[iG].cpu().numpy())[:, 4]
+    eS = np.abs(lamS[iS].double().cpu().numpy() - refS).max(axis=1)
+    eG = np.abs(lamG[iG].cpu().numpy() - refG).max(axis=1)
+    cpu = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{S64.shape[0]} symmetric + {G64.shape[0]} general matrices of the "
+                     f"mixed workload, eigenvalues + eigenvector-form gradient, "
+                     f"{dt:.2f} s wall on {threads} threads"}
+    err = {"f32c_sym6": float(np.max(eS / bS)), "f64_general9": float(np.max(eG / bG)),
+           "bound": "kappa ||A||_F u (u = 2^-24 for f32c, 2^-53 for f64; C = 1)",
+           "sample_matrices": int(S64.shape[0] + G64.shape[0])}
+    return cpu, err
+
+
+KERNELS = ("fwd_f64_general9", "bwd_f64_general9", "fwd_f32c_sym6", "bwd_f32c_sym6",
+           "fwd_f64_sym6")
+
+
+def run_single(args):
+    """W + K launches of one library kernel at size n (for profiler captures)."""
+    import paper_2511_00292_gb300 as eig3
+    from paper_2511_00292_gb300 import build as _b
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    _b.build()
+    n = args.n
+    if "general9" in args.only:
+        b = W.workload4(n=n, device=dev)
+        A, w = b.A, b.extra["w"]
+        prec = "f64"
+    else:
+        b = W.workload3(n=n, device=dev)
+        A, w = b.A, torch.randn(n, 3, dtype=torch.float32, device=dev)
+        prec = "f32c" if "f32c" in args.only else "f64"
+    lam, aux = eig3.eigvals(A, precision=prec, return_aux=True)
+    g = torch.empty_like(A)
+    st = eig3.Stats(dev)
+    if args.only.startswith("fwd"):
+        fn = lambda: eig3.eigvals(A, precision=prec, return_aux=True, out=lam, aux_out=aux,
+                                  stats=st)
+    else:
+        fn = lambda: eig3.eigvals_backward(A, w, aux=aux, precision=prec, out=g)
+    for _ in range(args.warmup):
+        fn()
+    ms = timed(fn, args.steps, torch.cuda.current_stream(dev))
+    print(json.dumps({"kernel": args.only, "n": n, "ms": ms, "G_matrices_per_s": n / ms / 1e6}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-paths", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--only", choices=KERNELS, default=None,
+                    help="time one kernel alone at size --n (profiler captures)")
+    ap.add_argument("--n", type=int, default=1 << 22)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.only:
+        return run_single(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

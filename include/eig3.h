@@ -1,0 +1,153 @@
+/*
+ * eig3.h -- C ABI of the GB300 (sm_103a) library for batched, numerically
+ * stable closed-form eigenvalues of real diagonalizable 3x3 matrices.
+ *
+ * Method: Habera & Zilian, "Numerically stable evaluation of closed-form
+ * expressions for eigenvalues of 3x3 matrices" (arXiv 2511.00292):
+ *   I1 (Algorithm 1) -> J2 (Algorithm 2) -> J3 (Algorithm 4)
+ *   -> Delta (Algorithm 5, sum of products) -> eigenvalues (Algorithm 6,
+ *   trigonometric formula with the arctangent triple angle, Eq. for phi).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers (memory of the current CUDA
+ *    device, e.g. from cudaMalloc or a torch CUDA tensor).  The caller owns
+ *    every buffer; the library never allocates, frees or synchronises.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL means the legacy default stream).  The returned status covers the
+ *    host-side argument checks and the launch (cudaGetLastError); errors of
+ *    the kernel itself surface at the caller's next synchronisation.
+ *  - Calls hold no host state between launches and read nothing back, so a
+ *    sequence of calls can be captured into a CUDA graph.
+ *  - n == 0 returns EIG3_OK without launching.  n < 0 or a NULL required
+ *    pointer with n > 0 returns EIG3_ERR_ARG; nothing is launched.
+ *  - Every pointer must be aligned to its element size (8 bytes for FP64,
+ *    4 for FP32), else EIG3_ERR_ALIGN.  Rows are packed: matrix i starts at
+ *    element 9*i (EIG3_GENERAL9) or 6*i (EIG3_SYM6).
+ *  - Non-finite input entries give non-finite outputs for that matrix; no
+ *    kernel traps.
+ *
+ * Layouts (`layout`)
+ *  EIG3_GENERAL9  row-major A00 A01 A02 A10 A11 A12 A20 A21 A22, 0-based
+ *                 indices as in the paper (Section "Invariant I1").
+ *  EIG3_SYM6      symmetric matrix stored as A00 A11 A22 A12 A02 A01 (Voigt
+ *                 order; the paper's symmetric routine does not fix one).
+ *
+ * Storage type (`dtype`) and arithmetic (`precision`)
+ *  EIG3_F64 + EIG3_PREC_F64        binary64 in, binary64 arithmetic, binary64 out.
+ *  EIG3_F32 + EIG3_PREC_F64        binary32 in, binary64 arithmetic, binary32 out.
+ *  EIG3_F32 + EIG3_PREC_F32_COMP   binary32 in, binary32 compensated arithmetic
+ *                                  (error-free TwoSum/TwoProduct transformations,
+ *                                  per-matrix power-of-two scaling of the
+ *                                  deviatoric part), binary32 out.  No binary64
+ *                                  arithmetic on this path except the binary64
+ *                                  invariants output of eig3_invariants.
+ *  EIG3_F64 + EIG3_PREC_F32_COMP   rejected with EIG3_ERR_DTYPE.
+ *
+ * Readings of the paper built into the library
+ *  - Algorithm 5, term r10: +M02*M21*d2 (the printed minus sign does not
+ *    reproduce the discriminant 4 J2^3 - 27 J3^2).
+ *  - Algorithm 6: phi = atan2(sqrt(27 Delta), 27 J3), in [0, pi].
+ *  - Computed J2 < 0 or Delta < 0 (possible for nonsymmetric input) are
+ *    clamped to 0 before the square roots.
+ *  - Output eigenvalues are ascending, lambda_1 <= lambda_2 <= lambda_3
+ *    (the ordering of the trigonometric formula, Section 1).
+ */
+#ifndef EIG3_H
+#define EIG3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EIG3_OK = 0,
+  EIG3_ERR_ARG = 1,    /* n < 0, or a required pointer is NULL while n > 0      */
+  EIG3_ERR_LAYOUT = 2, /* layout is not EIG3_GENERAL9 or EIG3_SYM6              */
+  EIG3_ERR_DTYPE = 3,  /* unsupported dtype / precision combination             */
+  EIG3_ERR_ALIGN = 4,  /* a pointer is not aligned to its element size          */
+  EIG3_ERR_CUDA = 5    /* the launch failed (cudaGetLastError after the launch) */
+} eig3_status;
+
+enum { EIG3_GENERAL9 = 0, EIG3_SYM6 = 1 };
+enum { EIG3_F64 = 0, EIG3_F32 = 1 };
+enum { EIG3_PREC_F64 = 0, EIG3_PREC_F32_COMP = 1 };
+
+/*
+ * Per-launch numerical statistics, accumulated on the device by
+ * eig3_eigvals when a non-NULL device pointer is passed.  Reset it with
+ * eig3_stats_reset before the first accumulating call.  40 bytes, 8-aligned.
+ * Several calls may accumulate into one struct (counts add, min/max combine).
+ */
+typedef struct {
+  unsigned long long n_delta_clamped; /* matrices whose computed Delta was < 0     */
+  unsigned long long n_j2_clamped;    /* matrices whose computed J2 was < 0        */
+  unsigned long long n_nonfinite;     /* matrices with a non-finite eigenvalue      */
+  double min_disc_ratio;              /* min over matrices with J2 > 0 of
+                                         Delta+/J2+^3 = 4 sin^2(phi), in [0, 4]
+                                         (0 at a repeated eigenvalue); evaluated in
+                                         binary32 from the computed triple angle */
+  double max_abs_lambda;              /* max over matrices of max_k |lambda_k|      */
+} eig3_stats;
+
+/*
+ * eig3_invariants -- the four invariants of Algorithms 1, 2, 4 and 5.
+ *   A    device, n matrices in `layout` / `dtype` (read only).
+ *   inv  device, n x 4 binary64, row i = (I1, J2, J3, Delta) of matrix i,
+ *        before any clamping (Delta may be slightly negative for
+ *        nonsymmetric input).  With EIG3_PREC_F32_COMP the compensated
+ *        binary32 values are returned unscaled in binary64.
+ */
+eig3_status eig3_invariants(const void *A, int layout, int dtype, int precision, int64_t n,
+                            double *inv, void *stream);
+
+/*
+ * eig3_eigvals -- ascending eigenvalues by Algorithm 6 on the stable invariants.
+ *   A      device, n matrices (read only).
+ *   lam    device, n x 3 of `dtype`: (lambda_1, lambda_2, lambda_3) per matrix.
+ *   aux    device, n x 4 of `dtype`, or NULL.  When given, receives the
+ *          values the adjoint needs, (r, sigma_1, sigma_2, I1) with
+ *          r = sqrt(3 J2+), sigma_1 = sin(phi/3), sigma_2 = sin((pi-phi)/3);
+ *          pass it back to eig3_eigvals_backward to skip the recomputation.
+ *   stats  device eig3_stats or NULL (see eig3_stats_reset).
+ */
+eig3_status eig3_eigvals(const void *A, int layout, int dtype, int precision, int64_t n,
+                         void *lam, void *aux, eig3_stats *stats, void *stream);
+
+/*
+ * eig3_eigvals_backward -- vector-Jacobian product of eig3_eigvals.
+ * Given grad_lam (dL/dlambda_k, n x 3 of `dtype`), writes
+ *   grad_A = dL/dA = a_I1 I + a_J2 dev(A)^T + a_J3 dev(cof(dev A))
+ * with a_I1 = sum_k g_k / 3 and (a_J2, a_J3) from the chain rule through the
+ * trigonometric formula (Jacobians of J2 and J3: Lemmas of Sections J2 and
+ * J3).  For EIG3_SYM6 the gradient is taken with respect to the six stored
+ * entries (an off-diagonal entry stands for both A_ij and A_ji, so it gets
+ * G_ij + G_ji).  Where two computed eigenvalues coincide exactly the
+ * individual eigenvalues are not differentiable; the weights of such a
+ * cluster are then replaced by their mean (the gradient of the cluster sum).
+ *   A         device, n matrices (read only).
+ *   grad_lam  device, n x 3 of `dtype` (read only).
+ *   aux       device n x 4 from eig3_eigvals on the same A, or NULL to
+ *             recompute it.
+ *   grad_A    device, n x 9 or n x 6 of `dtype`.
+ */
+eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int precision, int64_t n,
+                                  const void *grad_lam, const void *aux, void *grad_A,
+                                  void *stream);
+
+/* Set a device eig3_stats to (0, 0, 0, +inf, 0) on `stream`. */
+eig3_status eig3_stats_reset(eig3_stats *stats, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *eig3_status_string(int status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int eig3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIG3_H */

@@ -14,6 +14,7 @@ Function map (paper sections):
     eigvals           Algorithm 6 on the stable invariants
     eigvals_naive     Algorithm 6 on the naive invariants
     eigvals_grad      d lambda_k / dA = l r^T / (l^T r)  (Section 1, E_k^T)
+    eigval_jacobians  the three d lambda_k / dA separately
     bounds            first-order stability bounds, C = 1, Frobenius norm
     eigvals_mt        eigvals on POSIX threads, for timing on host cores
 """
@@ -67,6 +68,8 @@ def _load():
                 getattr(lib, name).restype = None
             lib.eig3o_eigvals_grad_batch.argtypes = [P, P, I64, I, P]
             lib.eig3o_eigvals_grad_batch.restype = None
+            lib.eig3o_eigval_jacobians_batch.argtypes = [P, I64, I, P]
+            lib.eig3o_eigval_jacobians_batch.restype = None
             lib.eig3o_bounds_batch.argtypes = [P, P, I64, I, D, P]
             lib.eig3o_bounds_batch.restype = None
             lib.eig3o_eigvals_batch_mt.argtypes = [P, I64, I, P, I]
@@ -129,6 +132,15 @@ def eigvals_grad(X, gbar, layout: int = GENERAL9) -> np.ndarray:
     out = np.empty_like(X)
     _load().eig3o_eigvals_grad_batch(_ptr(X), _ptr(g), X.shape[0], layout, _ptr(out))
     return out
+
+
+def eigval_jacobians(X, layout: int = GENERAL9) -> np.ndarray:
+    """(n, 3, 9): d lambda_k / dA_ij = l_i r_j / (l^T r) for each ascending
+    eigenvalue k, with respect to the 9 entries of the (expanded) matrix."""
+    X = _as_input(X, layout)
+    out = np.empty((X.shape[0], 27), dtype=np.float64)
+    _load().eig3o_eigval_jacobians_batch(_ptr(X), X.shape[0], layout, _ptr(out))
+    return out.reshape(-1, 3, 9)
 
 
 def bounds(X, kappa=None, layout: int = GENERAL9, u: float = U64) -> np.ndarray:

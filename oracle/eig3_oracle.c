@@ -387,6 +387,16 @@ void eig3o_eigvals_grad_batch(const double *X, const double *gbar, int64_t n, in
   }
 }
 
+/* d lambda_k / dA for every matrix: 27 doubles per matrix, k-major, row-major
+ * 3x3 blocks (with respect to the 9 entries of the expanded matrix). */
+void eig3o_eigval_jacobians_batch(const double *X, int64_t n, int layout, double *out) {
+  double A[9];
+  for (int64_t i = 0; i < n; ++i) {
+    load(X, i, layout, A);
+    eig3o_eigval_jacobians(A, out + 27 * i);
+  }
+}
+
 void eig3o_bounds_batch(const double *X, const double *kappa, int64_t n, int layout, double u,
                         double *out) {
   double A[9];

@@ -1,0 +1,164 @@
+"""Batched, numerically stable closed-form eigenvalues of real 3x3 matrices on
+GB300 (sm_103a), after Habera & Zilian, arXiv 2511.00292.
+
+Every step of the computation runs in the CUDA library ``libeig3.so``
+(include/eig3.h); this module only allocates outputs with torch and passes
+pointers and the current CUDA stream.  There is no CPU path: inputs must be
+CUDA tensors and the library must be built.
+
+Layouts: ``"general9"`` (n, 9) row-major, or (n, 3, 3); ``"sym6"`` (n, 6) in
+the order (A00, A11, A22, A12, A02, A01).
+Precisions: ``"f64"`` (binary64 arithmetic; storage float64 or float32) and
+``"f32c"`` (compensated binary32 arithmetic; storage float32).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (F32, F64, GENERAL9, PREC_F32_COMP, PREC_F64, SYM6, Eig3Error, Eig3Stats,
+                   check, load)
+
+__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "Stats", "Eig3Error",
+           "layout_of", "GENERAL9", "SYM6"]
+
+_LAYOUTS = {"general9": GENERAL9, "sym6": SYM6, GENERAL9: GENERAL9, SYM6: SYM6}
+_PRECS = {"f64": PREC_F64, "f32c": PREC_F32_COMP, PREC_F64: PREC_F64,
+          PREC_F32_COMP: PREC_F32_COMP}
+
+
+def layout_of(A: torch.Tensor, layout=None) -> int:
+    if layout is not None:
+        return _LAYOUTS[layout]
+    if A.dim() >= 2 and A.shape[-2:] == (3, 3):
+        return GENERAL9
+    if A.shape[-1] == 9:
+        return GENERAL9
+    if A.shape[-1] == 6:
+        return SYM6
+    raise ValueError(f"cannot infer the layout of a tensor of shape {tuple(A.shape)}")
+
+
+def _rows(A: torch.Tensor, layout: int) -> torch.Tensor:
+    w = 9 if layout == GENERAL9 else 6
+    if not A.is_cuda:
+        raise ValueError("eig3 runs on CUDA tensors only (no CPU path)")
+    if A.dtype not in (torch.float64, torch.float32):
+        raise TypeError(f"unsupported dtype {A.dtype}; use float64 or float32")
+    if not A.is_contiguous():
+        raise ValueError("A must be contiguous")
+    if A.numel() % w != 0:
+        raise ValueError(f"A has {A.numel()} elements, not a multiple of {w}")
+    return A.reshape(-1, w)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    return F64 if t.dtype == torch.float64 else F32
+
+
+def _stream(dev: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Stats:
+    """Device-resident eig3_stats accumulated by :func:`eigvals` (see eig3.h)."""
+
+    def __init__(self, device=None):
+        self.buf = torch.empty(5, dtype=torch.float64,
+                               device=device if device is not None else torch.device("cuda"))
+        self.reset()
+
+    def reset(self):
+        with torch.cuda.device(self.buf.device):
+            check(load().eig3_stats_reset(_ptr(self.buf), _stream(self.buf.device)),
+                  "eig3_stats_reset")
+
+    def read(self) -> dict:
+        raw = self.buf.cpu().numpy().tobytes()
+        s = Eig3Stats.from_buffer_copy(raw)
+        return {f: getattr(s, f) for f, _ in Eig3Stats._fields_}
+
+
+def invariants(A: torch.Tensor, layout=None, precision="f64") -> torch.Tensor:
+    """(n, 4) float64 tensor of (I1, J2, J3, Delta) (Algorithms 1, 2, 4, 5)."""
+    lay = layout_of(A, layout)
+    X = _rows(A, lay)
+    out = torch.empty((X.shape[0], 4), dtype=torch.float64, device=X.device)
+    with torch.cuda.device(X.device):
+        st = load().eig3_invariants(_ptr(X), lay, _dtype_code(X), _PRECS[precision], X.shape[0],
+                                    _ptr(out), _stream(X.device))
+    check(st, "eig3_invariants")
+    return out
+
+
+def eigvals(A: torch.Tensor, layout=None, precision="f64", return_aux=False, stats=None,
+            out=None, aux_out=None):
+    """Ascending eigenvalues, (n, 3) in the storage dtype (Algorithm 6).
+
+    With ``return_aux`` also returns the (n, 4) adjoint inputs
+    (r, sin(phi/3), sin((pi-phi)/3), I1) for :func:`eigvals_backward`.
+    ``out`` / ``aux_out`` may supply preallocated outputs (CUDA-graph use).
+    """
+    lay = layout_of(A, layout)
+    X = _rows(A, lay)
+    n = X.shape[0]
+    lam = out if out is not None else torch.empty((n, 3), dtype=X.dtype, device=X.device)
+    aux = None
+    if return_aux:
+        aux = aux_out if aux_out is not None else torch.empty((n, 4), dtype=X.dtype,
+                                                              device=X.device)
+    sp = _ptr(stats.buf) if stats is not None else None
+    with torch.cuda.device(X.device):
+        st = load().eig3_eigvals(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n, _ptr(lam),
+                                 _ptr(aux), sp, _stream(X.device))
+    check(st, "eig3_eigvals")
+    return (lam, aux) if return_aux else lam
+
+
+def eigvals_backward(A: torch.Tensor, grad_lam: torch.Tensor, aux=None, layout=None,
+                     precision="f64", out=None) -> torch.Tensor:
+    """dL/dA (same shape and dtype as the stored rows) given dL/dlambda (n, 3)."""
+    lay = layout_of(A, layout)
+    X = _rows(A, lay)
+    g = grad_lam.contiguous()
+    if g.dtype != X.dtype or g.numel() != 3 * X.shape[0] or not g.is_cuda:
+        raise ValueError("grad_lam must be a CUDA (n, 3) tensor of the storage dtype")
+    if aux is not None and (aux.dtype != X.dtype or aux.numel() != 4 * X.shape[0]):
+        raise ValueError("aux must be the (n, 4) tensor returned by eigvals(return_aux=True)")
+    gA = out if out is not None else torch.empty_like(X)
+    with torch.cuda.device(X.device):
+        st = load().eig3_eigvals_backward(_ptr(X), lay, _dtype_code(X), _PRECS[precision],
+                                          X.shape[0], _ptr(g), _ptr(aux), _ptr(gA),
+                                          _stream(X.device))
+    check(st, "eig3_eigvals_backward")
+    return gA
+
+
+class _Eig3Fn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, layout, precision):
+        lam, aux = eigvals(A, layout=layout, precision=precision, return_aux=True)
+        ctx.save_for_backward(A, aux)
+        ctx.layout = layout
+        ctx.precision = precision
+        return lam
+
+    @staticmethod
+    def backward(ctx, grad_lam):
+        A, aux = ctx.saved_tensors
+        gA = eigvals_backward(A, grad_lam.contiguous(), aux=aux, layout=ctx.layout,
+                              precision=ctx.precision)
+        return gA.reshape(A.shape), None, None
+
+
+def eigvals_ad(A: torch.Tensor, layout=None, precision="f64") -> torch.Tensor:
+    """Differentiable eigenvalues: the backward pass is the library's adjoint kernel."""
+    lay = layout_of(A, layout)
+    lam = _Eig3Fn.apply(A.contiguous(), lay, precision)
+    return lam

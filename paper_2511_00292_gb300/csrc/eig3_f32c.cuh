@@ -1,0 +1,450 @@
+// eig3_f32c.cuh -- compensated binary32 evaluation of the invariants (I1, J2,
+// J3, Delta of Algorithms 1, 2, 4, 5) and of the eigenvalues (Algorithm 6),
+// one matrix per thread, no binary64 arithmetic.
+//
+// GB300 issues binary32 FMAs 64 times faster than binary64 ones, so this path
+// buys accuracy with extra binary32 operations instead:
+//   * error-free transformations: TwoSum (Knuth) and TwoProduct through the
+//     fused multiply-add; sums of products are accumulated in the manner of
+//     Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+//     Comput. 26 (2005) (Sum2 / Dot2: the result is as accurate as if computed
+//     in twice the working precision and then rounded);
+//   * the diagonal differences d0, d1, d2 are exact as (hi, lo) pairs;
+//   * per-matrix power-of-two scaling of the deviatoric data (the d's and the
+//     off-diagonal entries) so that its largest magnitude lies in [1, 2): no
+//     overflow or underflow in the degree-6 discriminant for any binary32 input
+//     scale, and the scaling itself is exact.  The triple angle does not depend
+//     on the scale; r = sqrt(3 J2) is scaled back exactly.
+// All arithmetic in the error-free parts uses the __f*_rn intrinsics so that
+// the compiler cannot contract it into FMAs (which would break exactness).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eig3 {
+namespace c32 {
+
+struct F2 {
+  float h, l;  // unevaluated sum h + l
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// (x.h + x.l) * z to first order: the product x.h z is split exactly, x.l z
+// is added to the low part.
+__device__ __forceinline__ F2 mul(F2 x, float z) {
+  const float p = __fmul_rn(x.h, z);
+  return {p, __fmaf_rn(x.l, z, __fmaf_rn(x.h, z, -p))};
+}
+
+// (x.h + x.l)(y.h + y.l) to first order (x.l y.l is below the working
+// precision squared).
+__device__ __forceinline__ F2 mul(F2 x, F2 y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = __fmaf_rn(x.h, y.h, -p);
+  return {p, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e))};
+}
+
+__device__ __forceinline__ F2 neg(F2 x) { return {-x.h, -x.l}; }
+
+__device__ __forceinline__ F2 scale2(F2 x, float p2) {  // exact: p2 is a power of two
+  return {__fmul_rn(x.h, p2), __fmul_rn(x.l, p2)};
+}
+
+// Sum2 accumulator: s holds the rounded running sum, c the exact rounding
+// errors of the additions plus the low parts of the terms.
+struct Sum {
+  float s, c;
+};
+
+__device__ __forceinline__ Sum start(F2 x) { return {x.h, x.l}; }
+
+__device__ __forceinline__ Sum operator+(Sum a, F2 x) {
+  const F2 t = two_sum(a.s, x.h);
+  return {t.h, __fadd_rn(a.c, __fadd_rn(t.l, x.l))};
+}
+
+__device__ __forceinline__ Sum operator-(Sum a, F2 x) { return a + neg(x); }
+
+__device__ __forceinline__ Sum operator-(Sum a) { return {-a.s, -a.c}; }
+
+__device__ __forceinline__ Sum operator+(Sum a, Sum b) {
+  const F2 t = two_sum(a.s, b.s);
+  return {t.h, __fadd_rn(__fadd_rn(a.c, b.c), t.l)};
+}
+
+__device__ __forceinline__ F2 done(Sum a) { return two_sum(a.s, a.c); }
+
+__device__ __forceinline__ float round1(F2 x) { return __fadd_rn(x.h, x.l); }
+
+// (x.h + x.l)^2 to first order, as a pair.
+__device__ __forceinline__ F2 sq(F2 x) {
+  const float p = __fmul_rn(x.h, x.h);
+  const float e = __fmaf_rn(x.h, x.h, -p);
+  return {p, __fmaf_rn(__fadd_rn(x.h, x.h), x.l, e)};
+}
+
+// Invariants in scaled form.  With s = 2^-e the scale:
+//   J2x6 = 6 J2 s^2, J3x27 = 27 J3 s^3, D = Delta s^6, I1 unscaled.
+struct InvC {
+  F2 I1, J2x6, J3x27, D;
+  int e;  // the scale exponent
+};
+
+// Exponent field of the largest magnitude among the deviatoric data; the
+// scale 2^(127 - E) maps it into [1, 2) (E clamped so the scale is normal).
+__device__ __forceinline__ int scale_exponent(float m0, float m1, float m2, float m3, float m4,
+                                              float m5, float m6, float m7, float m8) {
+  int b = __float_as_int(m0) & 0x7fffffff;
+  b = max(b, __float_as_int(m1) & 0x7fffffff);
+  b = max(b, __float_as_int(m2) & 0x7fffffff);
+  b = max(b, __float_as_int(m3) & 0x7fffffff);
+  b = max(b, __float_as_int(m4) & 0x7fffffff);
+  b = max(b, __float_as_int(m5) & 0x7fffffff);
+  b = max(b, __float_as_int(m6) & 0x7fffffff);
+  b = max(b, __float_as_int(m7) & 0x7fffffff);
+  b = max(b, __float_as_int(m8) & 0x7fffffff);
+  return min(b >> 23, 253);
+}
+
+__device__ __forceinline__ float pow2_from_field(int field) { return __int_as_float(field << 23); }
+
+// 2^e for the unscaling, e = E - 127 with E in [0, 253]; E = 0 (all data zero
+// or subnormal, scaled by 2^127) needs the subnormal 2^-127.
+__device__ __forceinline__ float unscale_pow2(int e) {
+  return e > -127 ? __int_as_float((e + 127) << 23) : __int_as_float(0x00400000);
+}
+
+// Diagonal differences as exact pairs, the trace as an exact pair.
+struct Diag {
+  F2 d0, d1, d2, I1;
+};
+
+__device__ __forceinline__ Diag diag_parts(float a00, float a11, float a22) {
+  Diag g;
+  g.d0 = two_sum(a00, -a11);
+  g.d1 = two_sum(a00, -a22);
+  g.d2 = two_sum(a11, -a22);
+  const F2 t = two_sum(a00, a11);
+  const F2 u = two_sum(t.h, a22);
+  g.I1 = two_sum(u.h, __fadd_rn(t.l, u.l));
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric matrix (A00, A11, A22, A12, A02, A01) with a = A01, b = A02,
+// c = A12.  The r_i of Algorithm 5 are summed term by term as the paper
+// writes them (every term a product of three factors), with the symmetric
+// identities r1 = 0, r2 = r7, r3 = r5, r4 = r6 and reading R1 for r10:
+//   r2  = -ab d2 + aa c - bb c         r3  = ac d1 - aa b + cc b
+//   r4  =  bc d0 + cc a - bb a
+//   r8  = (d0d1 c - cc c) + aa c - ab d1
+//   r9  = (d0d1 c - cc c) + bb c - ab d0
+//   r10 = (d1d2 a - aa a) + bc d2 + bb a
+//   r11 = (d1d2 a - aa a) + bc d1 + cc a
+//   r13 =  (d0d2 b + bb b) + ac d2 - aa b
+//   r12 = -(d0d2 b + bb b) + ac d0 + cc b
+//   r14 = d0d1d2 - aa d0 + bb d1 - cc d2
+//   Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ InvC invariants_sym_c(float a00, float a11, float a22, float c0,
+                                                 float b0, float a0) {
+  const Diag g = diag_parts(a00, a11, a22);
+  InvC o;
+  o.I1 = g.I1;
+  const int E = scale_exponent(g.d0.h, g.d1.h, g.d2.h, a0, b0, c0, 0.f, 0.f, 0.f);
+  o.e = E - 127;
+  const float sc = pow2_from_field(254 - E);
+  const F2 d0 = scale2(g.d0, sc), d1 = scale2(g.d1, sc), d2 = scale2(g.d2, sc);
+  const float a = __fmul_rn(a0, sc), b = __fmul_rn(b0, sc), c = __fmul_rn(c0, sc);
+  const F2 aa = two_prod(a, a), bb = two_prod(b, b), cc = two_prod(c, c);
+  const F2 ab = two_prod(a, b), ac = two_prod(a, c), bc = two_prod(b, c);
+  // Algorithm 2, times 6: (d0^2 + d1^2 + d2^2) + 6 (aa + bb + cc)
+  const F2 off = done(start(aa) + bb + cc);
+  const Sum dsq = start(sq(d0)) + sq(d1) + sq(d2);
+  o.J2x6 = done(dsq + mul(off, 6.0f));
+  // Algorithm 4, times 27: 27 * 2abc + 9 (aa t1 + bb t2 + cc t3) - t1 t2 t3
+  const F2 t1 = done(start(d1) + d2);
+  const F2 t2 = done(start(d0) - d2);
+  const F2 t3 = done(start(neg(d0)) - d1);
+  const F2 abc = mul(ab, c);
+  const F2 mixed = done(start(mul(aa, t1)) + mul(bb, t2) + mul(cc, t3));
+  o.J3x27 = done(start(mul(abc, 54.0f)) + mul(mixed, 9.0f) - mul(mul(t1, t2), t3));
+  // Algorithm 5
+  const F2 d0d1 = mul(d0, d1), d0d2 = mul(d0, d2), d1d2 = mul(d1, d2);
+  const F2 aac = mul(aa, c), bbc = mul(bb, c), aab = mul(aa, b), ccb = mul(cc, b);
+  const F2 cca = mul(cc, a), bba = mul(bb, a);
+  const F2 r2 = done(start(neg(mul(ab, d2))) + aac - bbc);
+  const F2 r3 = done(start(mul(ac, d1)) - aab + ccb);
+  const F2 r4 = done(start(mul(bc, d0)) + cca - bba);
+  const Sum s89 = start(mul(d0d1, c)) - mul(cc, c);
+  const F2 r8 = done(s89 + aac - mul(ab, d1));
+  const F2 r9 = done(s89 + bbc - mul(ab, d0));
+  const Sum s1011 = start(mul(d1d2, a)) - mul(aa, a);
+  const F2 r10 = done(s1011 + mul(bc, d2) + bba);
+  const F2 r11 = done(s1011 + mul(bc, d1) + cca);
+  const Sum s1213 = start(mul(d0d2, b)) + mul(bb, b);
+  const F2 r13 = done(s1213 + mul(ac, d2) - aab);
+  const F2 r12 = done(-s1213 + mul(ac, d0) + ccb);
+  const F2 r14 =
+      done(start(mul(d0d1, d2)) - mul(aa, d0) + mul(bb, d1) - mul(cc, d2));
+  const F2 g14 = done(start(sq(r2)) + sq(r3) + sq(r4));
+  const Sum g2 = start(sq(r8)) + sq(r9) + sq(r10) + sq(r11) + sq(r12) + sq(r13);
+  const F2 g2d = done(g2);
+  o.D = done(start(mul(g14, 14.0f)) + scale2(g2d, 2.0f) + sq(r14));
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// General matrix.  dx(M) of Algorithm 5 term by term (reading R1 for r10).
+// The products M01 M10, M02 M20, M12 M21 and the d-products are the same for
+// M = A and M = A^T and are formed once by the caller.
+// ---------------------------------------------------------------------------
+struct Shared {
+  F2 d0, d1, d2, d0d1, d0d2, d1d2, d0d1d2, p01, p02, p12;
+};
+
+struct R13 {
+  F2 r[13];  // r1 .. r13
+};
+
+__device__ __forceinline__ R13 dx_c(float M01, float M02, float M10, float M12, float M20,
+                                    float M21, const Shared &s) {
+  R13 o;
+  const F2 m0112 = two_prod(M01, M12), m0210 = two_prod(M02, M10);
+  const F2 m0102 = two_prod(M01, M02), m0101 = two_prod(M01, M01);
+  const F2 m0202 = two_prod(M02, M02), m0121 = two_prod(M01, M21);
+  const F2 m0221 = two_prod(M02, M21), m0212 = two_prod(M02, M12);
+  const F2 m1212 = two_prod(M12, M12);
+  // r1 = M01 M12 M20 - M02 M10 M21
+  o.r[0] = done(start(mul(m0112, M20)) - mul(m0210, M21));
+  // r2 = -M01 M02 d2 + M01^2 M12 - M02^2 M21
+  o.r[1] = done(start(neg(mul(m0102, s.d2))) + mul(m0101, M12) - mul(m0202, M21));
+  // r3 = M01 M21 d1 - M01^2 M20 + M02 M21^2
+  o.r[2] = done(start(mul(m0121, s.d1)) - mul(m0101, M20) + mul(m0221, M21));
+  // r4 = M02 M12 d0 + M01 M12^2 - M02^2 M10
+  o.r[3] = done(start(mul(m0212, s.d0)) + mul(m0112, M12) - mul(m0202, M10));
+  // r5 = M01 M12 d1 - M01 M02 M10 + M02 M12 M21
+  o.r[4] = done(start(mul(m0112, s.d1)) - mul(m0102, M10) + mul(m0212, M21));
+  // r6 = M02 M21 d0 - M01 M02 M20 + M01 M12 M21
+  o.r[5] = done(start(mul(m0221, s.d0)) - mul(m0102, M20) + mul(m0112, M21));
+  // r7 = -M02 M10 d2 + M01 M10 M12 - M02 M12 M20
+  o.r[6] = done(start(neg(mul(m0210, s.d2))) + mul(s.p01, M12) - mul(m0212, M20));
+  // r8 = M12 d0 d1 - M02 M10 d1 + M01 M10 M12 - M12^2 M21
+  // r9 = M12 d0 d1 - M02 M10 d0 + M02 M12 M20 - M12^2 M21
+  const Sum s89 = start(mul(s.d0d1, M12)) - mul(m1212, M21);
+  o.r[7] = done(s89 - mul(m0210, s.d1) + mul(s.p01, M12));
+  o.r[8] = done(s89 - mul(m0210, s.d0) + mul(m0212, M20));
+  // r10 = M01 d1 d2 + M02 M21 d2 + M01 M02 M20 - M01^2 M10
+  // r11 = M01 d1 d2 + M02 M21 d1 + M01 M12 M21 - M01^2 M10
+  const Sum s1011 = start(mul(s.d1d2, M01)) - mul(m0101, M10);
+  o.r[9] = done(s1011 + mul(m0221, s.d2) + mul(m0102, M20));
+  o.r[10] = done(s1011 + mul(m0221, s.d1) + mul(m0112, M21));
+  // r12 = -M02 d0 d2 + M01 M12 d0 + M02 M12 M21 - M02^2 M20
+  // r13 =  M02 d0 d2 + M01 M12 d2 - M01 M02 M10 + M02^2 M20
+  const Sum s1213 = start(mul(s.d0d2, M02)) + mul(m0202, M20);
+  o.r[11] = done(-s1213 + mul(m0112, s.d0) + mul(m0212, M21));
+  o.r[12] = done(s1213 + mul(m0112, s.d2) - mul(m0102, M10));
+  return o;
+}
+
+__device__ __forceinline__ InvC invariants_general_c(const float (&a)[9]) {
+  const Diag g = diag_parts(a[0], a[4], a[8]);
+  InvC o;
+  o.I1 = g.I1;
+  const int E = scale_exponent(g.d0.h, g.d1.h, g.d2.h, a[1], a[2], a[3], a[5], a[6], a[7]);
+  o.e = E - 127;
+  const float sc = pow2_from_field(254 - E);
+  Shared s;
+  s.d0 = scale2(g.d0, sc);
+  s.d1 = scale2(g.d1, sc);
+  s.d2 = scale2(g.d2, sc);
+  const float A01 = __fmul_rn(a[1], sc), A02 = __fmul_rn(a[2], sc), A10 = __fmul_rn(a[3], sc);
+  const float A12 = __fmul_rn(a[5], sc), A20 = __fmul_rn(a[6], sc), A21 = __fmul_rn(a[7], sc);
+  s.p01 = two_prod(A01, A10);
+  s.p02 = two_prod(A02, A20);
+  s.p12 = two_prod(A12, A21);
+  // Algorithm 2, times 6
+  const F2 off = done(start(s.p01) + s.p02 + s.p12);
+  o.J2x6 = done(start(sq(s.d0)) + sq(s.d1) + sq(s.d2) + mul(off, 6.0f));
+  // Algorithm 4, times 27
+  const F2 t1 = done(start(s.d1) + s.d2);
+  const F2 t2 = done(start(s.d0) - s.d2);
+  const F2 t3 = done(start(neg(s.d0)) - s.d1);
+  const F2 offd = done(start(mul(two_prod(A01, A12), A20)) + mul(two_prod(A02, A10), A21));
+  const F2 mixed = done(start(mul(s.p01, t1)) + mul(s.p02, t2) + mul(s.p12, t3));
+  o.J3x27 = done(start(mul(offd, 27.0f)) + mul(mixed, 9.0f) - mul(mul(t1, t2), t3));
+  // Algorithm 5
+  s.d0d1 = mul(s.d0, s.d1);
+  s.d0d2 = mul(s.d0, s.d2);
+  s.d1d2 = mul(s.d1, s.d2);
+  // r14 = d0 d1 d2 - M01 M10 d0 + M02 M20 d1 - M12 M21 d2 (same for A and A^T)
+  const F2 r14 =
+      done(start(mul(s.d0d1, s.d2)) - mul(s.p01, s.d0) + mul(s.p02, s.d1) - mul(s.p12, s.d2));
+  const R13 u = dx_c(A01, A02, A10, A12, A20, A21, s);
+  const R13 v = dx_c(A10, A20, A01, A21, A02, A12, s);
+  // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1)
+  const F2 g6 = done(start(mul(u.r[1], v.r[1])) + mul(u.r[2], v.r[2]) + mul(u.r[3], v.r[3]));
+  const F2 g8 = done(start(mul(u.r[4], v.r[4])) + mul(u.r[5], v.r[5]) + mul(u.r[6], v.r[6]));
+  const F2 g2 = done(start(mul(u.r[7], v.r[7])) + mul(u.r[8], v.r[8]) + mul(u.r[9], v.r[9]) +
+                     mul(u.r[10], v.r[10]) + mul(u.r[11], v.r[11]) + mul(u.r[12], v.r[12]));
+  o.D = done(start(mul(mul(u.r[0], v.r[0]), 9.0f)) + mul(g6, 6.0f) + scale2(g8, 8.0f) +
+             scale2(g2, 2.0f) + sq(r14));
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 6 in binary32 from the compensated invariants.  The folded
+// triple angle phi~ = atan2(y, |x|) in [0, pi/2] (x = 27 J3, y = sqrt(27
+// Delta+), reading R2) gives sigma1 = sin(phi/3) and sigma2 = sin((pi-phi)/3)
+// without cancellation; the eigenvalues follow as in the binary64 path:
+//   lambda_1 = I1/3 - k (sigma2 + 2 sigma1), lambda_2 = I1/3 + k (sigma1 - sigma2),
+//   lambda_3 = I1/3 + k (2 sigma2 + sigma1),  k = 2 r / (3 sqrt 3).
+// ---------------------------------------------------------------------------
+struct EigC {
+  float l1, l2, l3, r, sigma1, sigma2, I1;
+  bool j2_clamped, d_clamped;
+};
+
+__device__ __forceinline__ EigC eigvals_c(const InvC &v) {
+  EigC o;
+  const float j2x6 = round1(v.J2x6);
+  const float dd = round1(v.D);
+  o.j2_clamped = j2x6 < 0.0f;
+  o.d_clamped = dd < 0.0f;
+  const float p2e = unscale_pow2(v.e);
+  // r = sqrt(3 J2) = sqrt(J2x6 / 2) * 2^e
+  o.r = __fmul_rn(sqrtf(0.5f * fmaxf(j2x6, 0.0f)), p2e);
+  const float x = round1(v.J3x27);
+  const float y = sqrtf(27.0f * fmaxf(dd, 0.0f));
+  const float pt = atan2f(y, fabsf(x)) * (1.0f / 3.0f);
+  float st, ct;
+  sincosf(pt, &st, &ct);
+  st = fmaxf(st, 0.0f);
+  const float other = fmaf(0.86602540378443864676f, ct, -0.5f * st);
+  const bool pos = !(x < 0.0f);
+  o.sigma1 = pos ? st : other;
+  o.sigma2 = pos ? other : st;
+  o.I1 = round1(v.I1);
+  const float k = o.r * 0.38490017945975050967f;
+  const float i3 = __fdiv_rn(o.I1, 3.0f);
+  o.l1 = fmaf(-k, fmaf(2.0f, o.sigma1, o.sigma2), i3);
+  o.l2 = fmaf(k, o.sigma1 - o.sigma2, i3);
+  o.l3 = fmaf(k, fmaf(2.0f, o.sigma2, o.sigma1), i3);
+  return o;
+}
+
+// Unscaled binary64 invariants (I1, J2, J3, Delta) from the compensated pairs.
+__device__ __forceinline__ void invariants_out(const InvC &v, double *o) {
+  const double s = ldexp(1.0, v.e);
+  o[0] = (double)v.I1.h + (double)v.I1.l;
+  o[1] = ((double)v.J2x6.h + (double)v.J2x6.l) / 6.0 * (s * s);
+  o[2] = ((double)v.J3x27.h + (double)v.J3x27.l) / 27.0 * (s * s * s);
+  const double s3 = s * s * s;
+  o[3] = ((double)v.D.h + (double)v.D.l) * s3 * s3;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint in binary32 (same divided-difference form as the binary64 path).
+// The cofactors of dev(A) are 2x2 determinants, evaluated with Kahan's
+// FMA scheme (w = b c; e = fma(-b, c, w); det = fma(a, d, -w) + e), which is
+// accurate to a few ulps even under cancellation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float det2(float a, float d, float b, float c) {
+  const float w = __fmul_rn(b, c);
+  const float e = __fmaf_rn(-b, c, w);
+  return __fadd_rn(__fmaf_rn(a, d, -w), e);
+}
+
+struct AdjC {
+  float aI1, aJ2r, aJ3r2, inv_r;  // a_I1, r a_J2, r^2 a_J3, 1/r
+};
+
+// Divided-difference adjoint in units of r (see the binary64 path): no
+// intermediate over- or underflows whatever the scale of the matrix.
+__device__ __forceinline__ AdjC adjoint_c(float r, float sigma1, float sigma2, float g1, float g2,
+                                          float g3) {
+  const float k2 = 1.15470053837925152902f;  // 2 / sqrt 3
+  const float g12 = k2 * sigma1;
+  const float g23 = k2 * sigma2;
+  const float g13 = k2 * (sigma1 + sigma2);
+  const float D12 = (g12 != 0.0f) ? (g2 - g1) / g12 : 0.0f;
+  const float D23 = (g23 != 0.0f) ? (g3 - g2) / g23 : 0.0f;
+  AdjC o;
+  o.aJ3r2 = (g13 != 0.0f) ? (D23 - D12) / g13 : 0.0f;
+  o.aJ2r = fmaf(-0.38490017945975050967f * fmaf(2.0f, sigma1, sigma2), o.aJ3r2, D23);
+  o.aI1 = ((g1 + g2) + g3) * (1.0f / 3.0f);
+  // r below the normal range counts as a triple eigenvalue
+  o.inv_r = (r >= 1.17549435e-38f) ? 1.0f / r : 0.0f;
+  return o;
+}
+
+__device__ __forceinline__ void grad_general_c(const float (&a)[9], const AdjC &s, float (&G)[9]) {
+  const float ir = s.inv_r;
+  const F2 d0 = two_sum(a[0], -a[4]), d1 = two_sum(a[0], -a[8]), d2 = two_sum(a[4], -a[8]);
+  const float ir3 = ir * (1.0f / 3.0f);
+  const float S00 = round1(done(start(d0) + d1)) * ir3;
+  const float S11 = round1(done(start(d2) - d0)) * ir3;
+  const float S22 = -round1(done(start(d1) + d2)) * ir3;
+  const float S01 = a[1] * ir, S02 = a[2] * ir, S10 = a[3] * ir;
+  const float S12 = a[5] * ir, S20 = a[6] * ir, S21 = a[7] * ir;
+  const float C00 = det2(S11, S22, S12, S21);
+  const float C01 = det2(S12, S20, S10, S22);
+  const float C02 = det2(S10, S21, S11, S20);
+  const float C10 = det2(S02, S21, S01, S22);
+  const float C11 = det2(S00, S22, S02, S20);
+  const float C12 = det2(S01, S20, S00, S21);
+  const float C20 = det2(S01, S12, S02, S11);
+  const float C21 = det2(S02, S10, S00, S12);
+  const float C22 = det2(S00, S11, S01, S10);
+  const float tc = ((C00 + C11) + C22) * (1.0f / 3.0f);
+  const float b2 = s.aJ2r, b3 = s.aJ3r2;
+  G[0] = fmaf(b2, S00, fmaf(b3, C00 - tc, s.aI1));
+  G[1] = fmaf(b2, S10, b3 * C01);
+  G[2] = fmaf(b2, S20, b3 * C02);
+  G[3] = fmaf(b2, S01, b3 * C10);
+  G[4] = fmaf(b2, S11, fmaf(b3, C11 - tc, s.aI1));
+  G[5] = fmaf(b2, S21, b3 * C12);
+  G[6] = fmaf(b2, S02, b3 * C20);
+  G[7] = fmaf(b2, S12, b3 * C21);
+  G[8] = fmaf(b2, S22, fmaf(b3, C22 - tc, s.aI1));
+}
+
+__device__ __forceinline__ void grad_sym_c(const float (&s6)[6], const AdjC &s, float (&G)[6]) {
+  const float ir = s.inv_r;
+  const F2 d0 = two_sum(s6[0], -s6[1]), d1 = two_sum(s6[0], -s6[2]), d2 = two_sum(s6[1], -s6[2]);
+  const float ir3 = ir * (1.0f / 3.0f);
+  const float S00 = round1(done(start(d0) + d1)) * ir3;
+  const float S11 = round1(done(start(d2) - d0)) * ir3;
+  const float S22 = -round1(done(start(d1) + d2)) * ir3;
+  const float S12 = s6[3] * ir, S02 = s6[4] * ir, S01 = s6[5] * ir;
+  const float C00 = det2(S11, S22, S12, S12);
+  const float C11 = det2(S00, S22, S02, S02);
+  const float C22 = det2(S00, S11, S01, S01);
+  const float C12 = det2(S01, S02, S00, S12);
+  const float C02 = det2(S01, S12, S02, S11);
+  const float C01 = det2(S12, S02, S01, S22);
+  const float tc = ((C00 + C11) + C22) * (1.0f / 3.0f);
+  const float b2 = s.aJ2r, b3 = s.aJ3r2;
+  const float b2x2 = 2.0f * b2, b3x2 = 2.0f * b3;
+  G[0] = fmaf(b2, S00, fmaf(b3, C00 - tc, s.aI1));
+  G[1] = fmaf(b2, S11, fmaf(b3, C11 - tc, s.aI1));
+  G[2] = fmaf(b2, S22, fmaf(b3, C22 - tc, s.aI1));
+  G[3] = fmaf(b2x2, S12, b3x2 * C12);
+  G[4] = fmaf(b2x2, S02, b3x2 * C02);
+  G[5] = fmaf(b2x2, S01, b3x2 * C01);
+}
+
+}  // namespace c32
+}  // namespace eig3

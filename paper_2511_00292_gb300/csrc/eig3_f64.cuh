@@ -1,0 +1,413 @@
+// eig3_f64.cuh -- binary64 device arithmetic of the closed-form 3x3 eigenvalue
+// method (Habera & Zilian, arXiv 2511.00292), one matrix per thread.
+//
+// Everything here is written for the GB300 FP64 pipe, which issues about two
+// DFMA per SM per clock (64x below FP32): every DADD/DMUL/DFMA counts, so the
+// algorithms are evaluated with fused multiply-adds and with products shared
+// between the invariants, between dx(A) and dx(A^T), and between the terms of
+// Algorithm 5.  The numerical structure of the paper is kept: the diagonal
+// enters only through the differences d0, d1, d2, every r_i of Algorithm 5
+// is a sum of products of small factors, and the discriminant is the weighted
+// sum of products u_i v_i.  Only the grouping of the products changes, which
+// moves rounding errors by a few units in the last place.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eig3 {
+
+// Constants (binary64 nearest values).
+constexpr double kInv3 = 0.333333333333333314829616256247390992939472198486328125;
+constexpr double kInv6 = 0.1666666666666666574148081281236954964697360992431640625;
+constexpr double kInv27 = 0.037037037037037034981127388472299207933247089385986328125;
+constexpr double kHalfSqrt3 = 0.86602540378443859658830206171842291951179504394531250;
+constexpr double kTwoOverSqrt3 = 1.1547005383792514621144972236652486026287078857421875;
+// 2 / (3 sqrt 3): eigenvalue offsets are k * (...) with k = r * kK
+constexpr double kK = 0.38490017945975052082056230772286653518676757812500;
+
+// Invariants of one matrix.  J2, J3 and D are those of 2^-e A (e = 0 unless
+// the deviatoric data was out of the safe exponent range, see dev_scale).
+struct Inv {
+  double I1, J2, J3, D;
+  int e;
+};
+
+// Power-of-two scaling of the deviatoric data (the diagonal differences and
+// the off-diagonal entries).  Delta is of degree 6 in these, so without it
+// Delta underflows once their magnitude m drops below about 1e-51 (and
+// overflows above 1e51), and the triple angle is lost.  When the largest
+// exponent lies outside [2^-150, 2^150) the data is multiplied by 2^-e so that
+// m lies in [1, 2); the angle does not depend on the scale and r is scaled
+// back exactly.  The test is a few integer operations on the high words; the
+// nine multiplications only run for matrices that need them.
+__device__ __forceinline__ int hi_abs(double x) { return __double2hiint(x) & 0x7fffffff; }
+
+__device__ __forceinline__ double pow2d(int k) {  // 2^k for -1022 <= k <= 1023
+  return __hiloint2double((k + 1023) << 20, 0);
+}
+
+template <int N>
+__device__ __forceinline__ int dev_scale(double (&v)[N]) {
+  int h = hi_abs(v[0]);
+#pragma unroll
+  for (int j = 1; j < N; ++j) h = max(h, hi_abs(v[j]));
+  const int E = h >> 20;  // biased exponent of the largest magnitude
+  int e = 0;
+  if (E < 1023 - 150 || E >= 1023 + 150) {
+    e = min(max(E, 1), 2045) - 1023;  // zero / subnormal data: scale by 2^1022
+    const double sc = pow2d(-e);
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] *= sc;
+  }
+  return e;
+}
+
+// --------------------------------------------------------------------------
+// General 9-entry matrix: Algorithms 1, 2, 4, 5.
+// --------------------------------------------------------------------------
+//
+// dx(M) of Algorithm 5 for M = A and M = A^T.  Products that are the same for
+// A and A^T (A01 A10, A02 A20, A12 A21, products of the d's) are formed once.
+// Reading R1 (r10 = M01 d1 d2 + M02 M21 d2 + M01 M02 M20 - M01^2 M10) applies.
+//
+// Factored forms used below (each is the paper's r_i regrouped, no terms
+// dropped; the diagonal still enters only through d0, d1, d2):
+//   r1  = (M01 M12) M20 - (M02 M10) M21
+//   r2  = M01 X - M02 (M02 M21),              X = M01 M12 - M02 d2
+//   r3  = M01 (M21 d1 - M01 M20) + M21 (M02 M21)
+//   r4  = M12 (M02 d0 + M01 M12) - M02 (M02 M10)
+//   r5  = M01 Y + M12 (M02 M21),              Y = M12 d1 - M02 M10
+//   r6  = M02 (M21 d0 - M01 M20) + M21 (M01 M12)
+//   r7  = M10 X - M12 (M02 M20)
+//   r8  = d1 (M12 d0 - M02 M10) + M12 (M01 M10 - M12 M21)
+//   r9  = d0 Y + M12 (M02 M20 - M12 M21)
+//   r10 = M01 (d1 d2 + M02 M20 - M01 M10) + d2 (M02 M21)
+//   r11 = M01 (d1 d2 + M12 M21 - M01 M10) + d1 (M02 M21)
+//   r12 = M02 (M12 M21 - M02 M20 - d0 d2) + d0 (M01 M12)
+//   r13 = M02 (d0 d2 + M02 M20 - M01 M10) + d2 (M01 M12)
+//   r14 = d0 (d1 d2 - M01 M10) + d1 (M02 M20) - d2 (M12 M21)   (same for A^T)
+struct DxShared {
+  double d0, d1, d2;
+  double p01, p02, p12;  // A01 A10, A02 A20, A12 A21
+  double e8, e9;         // p01 - p12, p02 - p12
+  double q10, q11, q12, q13;
+};
+
+struct Dx {
+  double r1, r2, r3, r4, r5, r6, r7, r8, r9, r10, r11, r12, r13;
+};
+
+__device__ __forceinline__ Dx dx13(double M01, double M02, double M10, double M12, double M20,
+                                   double M21, const DxShared &s) {
+  Dx r;
+  const double m0112 = M01 * M12;
+  const double m0210 = M02 * M10;
+  const double m0221 = M02 * M21;
+  const double m0120 = M01 * M20;
+  const double X = fma(-M02, s.d2, m0112);
+  const double Y = fma(M12, s.d1, -m0210);
+  r.r1 = fma(m0112, M20, -(m0210 * M21));
+  r.r2 = fma(M01, X, -(M02 * m0221));
+  r.r3 = fma(M01, fma(M21, s.d1, -m0120), M21 * m0221);
+  r.r4 = fma(M12, fma(M02, s.d0, m0112), -(M02 * m0210));
+  r.r5 = fma(M01, Y, M12 * m0221);
+  r.r6 = fma(M02, fma(M21, s.d0, -m0120), M21 * m0112);
+  r.r7 = fma(M10, X, -(M12 * s.p02));
+  r.r8 = fma(s.d1, fma(M12, s.d0, -m0210), M12 * s.e8);
+  r.r9 = fma(s.d0, Y, M12 * s.e9);
+  r.r10 = fma(M01, s.q10, s.d2 * m0221);
+  r.r11 = fma(M01, s.q11, s.d1 * m0221);
+  r.r12 = fma(M02, s.q12, s.d0 * m0112);
+  r.r13 = fma(M02, s.q13, s.d2 * m0112);
+  return r;
+}
+
+// a[0..8] row-major.  Returns the four invariants (unclamped).
+__device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
+  const double a00 = a[0], a11 = a[4], a22 = a[8];
+  Inv o;
+  // Algorithm 1
+  o.I1 = (a00 + a11) + a22;
+  // diagonal differences (shared by Algorithms 2, 4, 5), then the scaling
+  double sv[9] = {a00 - a11, a00 - a22, a11 - a22, a[1], a[2], a[3], a[5], a[6], a[7]};
+  o.e = dev_scale<9>(sv);
+  DxShared s;
+  s.d0 = sv[0];
+  s.d1 = sv[1];
+  s.d2 = sv[2];
+  const double a01 = sv[3], a02 = sv[4], a10 = sv[5], a12 = sv[6], a20 = sv[7], a21 = sv[8];
+  s.p01 = a01 * a10;
+  s.p02 = a02 * a20;
+  s.p12 = a12 * a21;
+  // Algorithm 2: diag/6 + offdiag
+  o.J2 = fma(fma(s.d0, s.d0, fma(s.d1, s.d1, s.d2 * s.d2)), kInv6, (s.p01 + s.p02) + s.p12);
+  // Algorithm 4: offdiag + mixed/3 - t1 t2 t3 / 27
+  const double t1 = s.d1 + s.d2;
+  const double t2 = s.d0 - s.d2;
+  const double t3 = -s.d0 - s.d1;
+  const double offdiag = fma(a01 * a12, a20, (a02 * a10) * a21);
+  const double mixed = fma(s.p01, t1, fma(s.p02, t2, s.p12 * t3));
+  o.J3 = fma(-(t1 * t2), t3 * kInv27, fma(mixed, kInv3, offdiag));
+  // Algorithm 5 (reading R1 for r10)
+  const double d1d2 = s.d1 * s.d2;
+  const double d0d2 = s.d0 * s.d2;
+  s.e8 = s.p01 - s.p12;
+  s.e9 = s.p02 - s.p12;
+  const double f0201 = s.p02 - s.p01;
+  s.q10 = d1d2 + f0201;
+  s.q11 = d1d2 + (s.p12 - s.p01);
+  s.q12 = (s.p12 - s.p02) - d0d2;
+  s.q13 = d0d2 + f0201;
+  const double r14 = fma(s.d0, d1d2 - s.p01, fma(s.d1, s.p02, -(s.d2 * s.p12)));
+  const Dx u = dx13(a01, a02, a10, a12, a20, a21, s);
+  const Dx v = dx13(a10, a20, a01, a21, a02, a12, s);
+  // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1), grouped by weight
+  const double g6 = fma(u.r2, v.r2, fma(u.r3, v.r3, u.r4 * v.r4));
+  const double g8 = fma(u.r5, v.r5, fma(u.r6, v.r6, u.r7 * v.r7));
+  const double g2 = fma(u.r8, v.r8,
+                        fma(u.r9, v.r9,
+                            fma(u.r10, v.r10, fma(u.r11, v.r11, fma(u.r12, v.r12, u.r13 * v.r13)))));
+  o.D = fma(9.0 * u.r1, v.r1, fma(6.0, g6, fma(8.0, g8, fma(2.0, g2, r14 * r14))));
+  return o;
+}
+
+// --------------------------------------------------------------------------
+// Symmetric matrix, stored (A00, A11, A22, A12, A02, A01).
+// With A = A^T, dx(A) = dx(A^T), r1 = 0, r2 = r7, r3 = r5, r4 = r6, so
+// Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
+  const double a00 = s6[0], a11 = s6[1], a22 = s6[2];
+  Inv o;
+  o.I1 = (a00 + a11) + a22;
+  double sv[6] = {a00 - a11, a00 - a22, a11 - a22, s6[3], s6[4], s6[5]};
+  o.e = dev_scale<6>(sv);
+  const double d0 = sv[0], d1 = sv[1], d2 = sv[2];
+  const double c = sv[3];  // A12
+  const double b = sv[4];  // A02
+  const double a = sv[5];  // A01
+  const double aa = a * a, bb = b * b, cc = c * c;
+  const double ab = a * b, ac = a * c, bc = b * c;
+  o.J2 = fma(fma(d0, d0, fma(d1, d1, d2 * d2)), kInv6, (aa + bb) + cc);
+  const double t1 = d1 + d2, t2 = d0 - d2, t3 = -d0 - d1;
+  const double offdiag = 2.0 * (ab * c);
+  const double mixed = fma(aa, t1, fma(bb, t2, cc * t3));
+  o.J3 = fma(-(t1 * t2), t3 * kInv27, fma(mixed, kInv3, offdiag));
+  const double d1d2 = d1 * d2, d0d2 = d0 * d2;
+  const double fba = bb - aa;
+  const double r2 = fma(a, fma(-b, d2, ac), -(b * bc));
+  const double r3 = fma(a, fma(c, d1, -ab), c * bc);
+  const double r4 = fma(c, fma(b, d0, ac), -(b * ab));
+  const double r8 = fma(d1, fma(c, d0, -ab), c * (aa - cc));
+  const double r9 = fma(d0, fma(c, d1, -ab), c * (bb - cc));
+  const double r10 = fma(a, d1d2 + fba, d2 * bc);
+  const double r11 = fma(a, d1d2 + (cc - aa), d1 * bc);
+  const double r12 = fma(b, (cc - bb) - d0d2, d0 * ac);
+  const double r13 = fma(b, d0d2 + fba, d2 * ac);
+  const double r14 = fma(d0, d1d2 - aa, fma(d1, bb, -(d2 * cc)));
+  const double g14 = fma(r2, r2, fma(r3, r3, r4 * r4));
+  const double g2 =
+      fma(r8, r8, fma(r9, r9, fma(r10, r10, fma(r11, r11, fma(r12, r12, r13 * r13)))));
+  o.D = fma(14.0, g14, fma(2.0, g2, r14 * r14));
+  return o;
+}
+
+// --------------------------------------------------------------------------
+// Algorithm 6, angle part.  With x = 27 J3 and y = sqrt(27 Delta+) the triple
+// angle is phi = atan2(y, x) in [0, pi] (reading R2).  The kernel needs
+//   sigma1 = sin(phi / 3)          and   sigma2 = sin((pi - phi) / 3),
+// from which cos(phi/3) = (2 sigma2 + sigma1) / sqrt 3 and the three
+// eigenvalues follow without cancellation, and which are also the adjoint's
+// eigenvalue gaps (lambda2 - lambda1 and lambda3 - lambda2, up to 2r/sqrt3).
+//
+// The folded angle phi~ = atan2(y, |x|) in [0, pi/2] is phi when x >= 0 and
+// pi - phi when x < 0, so both sigmas come from psi~ = phi~/3 in [0, pi/6]:
+// the small one is sin(psi~) and the other sin(pi/3 - psi~).
+//
+// cos(psi~) + i sin(psi~) is the principal cube root of z / |z| with
+// z = |x| + i y.  It is obtained without a binary64 arctangent or sine: a
+// binary32 seed w0 = e^{i psi0} (atan2f and __sincosf on the power-of-two
+// scaled z) is rotated by eps = arg(z conj(w0)^3) / 3, the Newton correction
+// of the cube root on the unit circle, and renormalised.  With |3 eps| below
+// about 1e-5 the neglected terms (eps^3, and t^3 in arg = t - t^3/3) are
+// below 1e-17, so the result carries binary64 accuracy; the conditioning is
+// that of phi itself (the three cube roots are 120 degrees apart).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void triple_angle_sines(double x, double y, double &sigma1,
+                                                   double &sigma2) {
+  const double ax = fabs(x);
+  // 2^(1023 - e) with e the exponent field of max(|x|, y): scaled max in [1, 2)
+  const int h = max(__double2hiint(ax), __double2hiint(y));
+  const int e = min((h >> 20) & 0x7ff, 2045);
+  const double sc = __hiloint2double((2046 - e) << 20, 0);
+  const double X = ax * sc, Y = y * sc;
+  // binary32 seed
+  const float pf = atan2f(__double2float_rn(Y), __double2float_rn(X)) * (1.0f / 3.0f);
+  float sf, cf;
+  __sincosf(pf, &sf, &cf);
+  const double c0 = (double)cf, s0 = (double)sf;
+  // w0^3
+  const double a2 = fma(c0, c0, -(s0 * s0));
+  const double b2 = (c0 + c0) * s0;
+  const double a3 = fma(a2, c0, -(b2 * s0));
+  const double b3 = fma(a2, s0, b2 * c0);
+  // rho = z conj(w0^3); its argument is 3 eps
+  const double re = fma(X, a3, Y * b3);
+  const double im = fma(Y, a3, -(X * b3));
+  const double rc0 = (double)__frcp_rn(__double2float_rn(re));
+  const double rc = fma(rc0, fma(-re, rc0, 1.0), rc0);
+  double eps = (im * rc) * kInv3;
+  eps = (re > 0.0) ? eps : 0.0;  // z = 0: the angle is undetermined, keep phi = 0
+  // w1 = w0 e^{i eps}, then |w1| -> 1
+  const double ce = fma(-0.5 * eps, eps, 1.0);
+  const double c1 = fma(c0, ce, -(s0 * eps));
+  const double s1 = fma(s0, ce, c0 * eps);
+  const double eta = fma(c1, c1, s1 * s1) - 1.0;
+  const double f = fma(eta, fma(eta, 0.375, -0.5), 1.0);
+  const double ct = c1 * f;
+  const double st = fmax(s1 * f, 0.0);
+  const double other = fma(kHalfSqrt3, ct, -0.5 * st);  // sin(pi/3 - psi~)
+  const bool pos = !(x < 0.0);
+  sigma1 = pos ? st : other;
+  sigma2 = pos ? other : st;
+}
+
+// Algorithm 6, eigenvalues: lambda_k = I1/3 + (2/3) r cos((phi + 2 pi k)/3),
+// r = sqrt(3 J2+), written with the sigmas:
+//   lambda_1 = I1/3 - k (sigma2 + 2 sigma1)
+//   lambda_2 = I1/3 + k (sigma1 - sigma2)
+//   lambda_3 = I1/3 + k (2 sigma2 + sigma1),     k = 2 r / (3 sqrt 3).
+// With sigma1, sigma2 >= 0 and monotone rounding the order
+// lambda_1 <= lambda_2 <= lambda_3 holds exactly.
+struct Eig {
+  double l1, l2, l3;  // ascending
+  double r, sigma1, sigma2;
+  bool j2_clamped, d_clamped;
+};
+
+__device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
+  Eig o;
+  o.j2_clamped = v.J2 < 0.0;
+  o.d_clamped = v.D < 0.0;
+  const double J2p = fmax(v.J2, 0.0);
+  const double Dp = fmax(v.D, 0.0);
+  o.r = sqrt(3.0 * J2p);
+  if (v.e != 0) o.r *= pow2d(v.e);
+  triple_angle_sines(27.0 * v.J3, sqrt(27.0 * Dp), o.sigma1, o.sigma2);
+  const double k = o.r * kK;
+  const double i3 = v.I1 * kInv3;
+  o.l1 = fma(-k, fma(2.0, o.sigma1, o.sigma2), i3);
+  o.l2 = fma(k, o.sigma1 - o.sigma2, i3);
+  o.l3 = fma(k, fma(2.0, o.sigma2, o.sigma1), i3);
+  return o;
+}
+
+// --------------------------------------------------------------------------
+// Adjoint.  lambda_k = I1/3 + mu_k with mu_k the roots of mu^3 - J2 mu - J3
+// (the trigonometric formula solves exactly this depressed cubic).  The chain
+// rule through I1, J2, J3 gives
+//   dL/dA = a_I1 I + a_J2 dev(A)^T + a_J3 dev(cof(dev A))
+// (Jacobians of J2 and J3 from the Lemmas of Sections J2 and J3) with
+//   a_I1 = sum_k g_k / 3,
+//   a_J2 = sum_k g_k mu_k / p'(mu_k),   a_J3 = sum_k g_k / p'(mu_k),
+// p'(mu_k) = prod_{j != k} (mu_k - mu_j).  These are divided differences of
+// the weights over the nodes mu_1 <= mu_2 <= mu_3:
+//   a_J3 = g[mu1, mu2, mu3] = (D23 - D12) / (mu3 - mu1),
+//   a_J2 = mu1 a_J3 + D23,   D12 = (g2 - g1)/(mu2 - mu1), D23 = (g3 - g2)/(mu3 - mu2).
+// The gaps come straight from the angle: mu2 - mu1 = (2r/sqrt3) sigma1,
+// mu3 - mu2 = (2r/sqrt3) sigma2, mu3 - mu1 = (2r/sqrt3)(sigma1 + sigma2), so
+// a coalescing pair enters only through the difference of its weights.
+// Where a computed gap is exactly 0 the pair's divided difference is taken as
+// 0, i.e. the cluster's weights are replaced by their mean; r = 0 (a triple
+// eigenvalue) leaves a_I1 I.
+//
+// Everything is carried in units of r: with S^ = dev(A)/r,
+//   a_J2 dev(A)^T = (r a_J2) S^T,   a_J3 dev(cof dev A) = (r^2 a_J3) dev(cof S^),
+// and r a_J2, r^2 a_J3 depend only on the sigmas and the weights, so no
+// intermediate over- or underflows for matrices of any scale.
+// --------------------------------------------------------------------------
+struct Adj {
+  double aI1, aJ2r, aJ3r2, inv_r;
+};
+
+__device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double sigma2, double g1,
+                                               double g2, double g3) {
+  const double g12 = kTwoOverSqrt3 * sigma1;
+  const double g23 = kTwoOverSqrt3 * sigma2;
+  const double g13 = kTwoOverSqrt3 * (sigma1 + sigma2);
+  const double D12 = (g12 != 0.0) ? (g2 - g1) / g12 : 0.0;
+  const double D23 = (g23 != 0.0) ? (g3 - g2) / g23 : 0.0;
+  Adj o;
+  o.aJ3r2 = (g13 != 0.0) ? (D23 - D12) / g13 : 0.0;
+  o.aJ2r = fma(-kK * fma(2.0, sigma1, sigma2), o.aJ3r2, D23);
+  o.aI1 = ((g1 + g2) + g3) * kInv3;
+  // r below the normal range counts as a triple eigenvalue
+  o.inv_r = (r >= 2.2250738585072014e-308) ? 1.0 / r : 0.0;
+  return o;
+}
+
+// Gradient of a general matrix from the adjoint scalars, G[0..8] row-major.
+__device__ __forceinline__ void grad_general(const double (&a)[9], const Adj &s, double (&G)[9]) {
+  const double ir = s.inv_r;
+  const double d0 = a[0] - a[4], d1 = a[0] - a[8], d2 = a[4] - a[8];
+  // S = dev(A) / r: diagonal from the differences, exact for A = alpha I
+  const double ir3 = ir * kInv3;
+  const double S00 = (d0 + d1) * ir3;
+  const double S11 = (d2 - d0) * ir3;
+  const double S22 = -(d1 + d2) * ir3;
+  const double S01 = a[1] * ir, S02 = a[2] * ir, S10 = a[3] * ir;
+  const double S12 = a[5] * ir, S20 = a[6] * ir, S21 = a[7] * ir;
+  // C = cof(S)
+  const double C00 = fma(S11, S22, -(S12 * S21));
+  const double C01 = fma(S12, S20, -(S10 * S22));
+  const double C02 = fma(S10, S21, -(S11 * S20));
+  const double C10 = fma(S02, S21, -(S01 * S22));
+  const double C11 = fma(S00, S22, -(S02 * S20));
+  const double C12 = fma(S01, S20, -(S00 * S21));
+  const double C20 = fma(S01, S12, -(S02 * S11));
+  const double C21 = fma(S02, S10, -(S00 * S12));
+  const double C22 = fma(S00, S11, -(S01 * S10));
+  const double tc = ((C00 + C11) + C22) * kInv3;
+  const double b2 = s.aJ2r, b3 = s.aJ3r2;
+  // G = aI1 I + (r aJ2) S^T + (r^2 aJ3) (C - tc I)
+  G[0] = fma(b2, S00, fma(b3, C00 - tc, s.aI1));
+  G[1] = fma(b2, S10, b3 * C01);
+  G[2] = fma(b2, S20, b3 * C02);
+  G[3] = fma(b2, S01, b3 * C10);
+  G[4] = fma(b2, S11, fma(b3, C11 - tc, s.aI1));
+  G[5] = fma(b2, S21, b3 * C12);
+  G[6] = fma(b2, S02, b3 * C20);
+  G[7] = fma(b2, S12, b3 * C21);
+  G[8] = fma(b2, S22, fma(b3, C22 - tc, s.aI1));
+}
+
+// Gradient with respect to the six stored entries of a symmetric matrix:
+// diagonal G_ii, off-diagonal G_ij + G_ji = 2 (aJ2 S_ij + aJ3 C_ij) (S and
+// cof(S) are symmetric).  Output order (A00, A11, A22, A12, A02, A01).
+__device__ __forceinline__ void grad_sym(const double (&s6)[6], const Adj &s, double (&G)[6]) {
+  const double ir = s.inv_r;
+  const double d0 = s6[0] - s6[1], d1 = s6[0] - s6[2], d2 = s6[1] - s6[2];
+  const double ir3 = ir * kInv3;
+  const double S00 = (d0 + d1) * ir3;
+  const double S11 = (d2 - d0) * ir3;
+  const double S22 = -(d1 + d2) * ir3;
+  const double S12 = s6[3] * ir, S02 = s6[4] * ir, S01 = s6[5] * ir;
+  const double C00 = fma(S11, S22, -(S12 * S12));
+  const double C11 = fma(S00, S22, -(S02 * S02));
+  const double C22 = fma(S00, S11, -(S01 * S01));
+  const double C12 = fma(S01, S02, -(S00 * S12));
+  const double C02 = fma(S01, S12, -(S02 * S11));
+  const double C01 = fma(S12, S02, -(S01 * S22));
+  const double tc = ((C00 + C11) + C22) * kInv3;
+  const double b2 = s.aJ2r, b3 = s.aJ3r2;
+  const double b2x2 = 2.0 * b2, b3x2 = 2.0 * b3;
+  G[0] = fma(b2, S00, fma(b3, C00 - tc, s.aI1));
+  G[1] = fma(b2, S11, fma(b3, C11 - tc, s.aI1));
+  G[2] = fma(b2, S22, fma(b3, C22 - tc, s.aI1));
+  G[3] = fma(b2x2, S12, b3x2 * C12);
+  G[4] = fma(b2x2, S02, b3x2 * C02);
+  G[5] = fma(b2x2, S01, b3x2 * C01);
+}
+
+}  // namespace eig3

@@ -1,0 +1,258 @@
+"""GPU edge cases: empty and ragged batches, degenerate matrices, non-finite
+entries, extreme scales, misaligned pointers, output guard bands, the
+statistics struct, and capture of the whole forward + backward step in a
+CUDA graph."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+GEN, SYM = 0, 1
+
+
+@pytest.fixture(scope="module")
+def eig3():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_00292_gb300 as m
+    return m
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def test_empty_batch(eig3):
+    for prec, dt in (("f64", torch.float64), ("f32c", torch.float32)):
+        A = torch.empty(0, 9, dtype=dt, device=dev())
+        assert eig3.eigvals(A, precision=prec).shape == (0, 3)
+        assert eig3.invariants(A, precision=prec).shape == (0, 4)
+        g = torch.empty(0, 3, dtype=dt, device=dev())
+        assert eig3.eigvals_backward(A, g, precision=prec).shape == (0, 9)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 256, 257, 1025, 38913])
+def test_ragged_sizes(eig3, n):
+    bt = W.workload2(n=n, device="cpu", seed=1500 + n)
+    lam = U.to_np(eig3.eigvals(bt.A.to(dev())))
+    err, tol, bad = U.check_eig_f64(lam, bt.A.numpy(), bt.kappa.numpy(), GEN)
+    assert not bad.any()
+    S = W.workload3(n=n, device="cpu", seed=1600 + n)
+    lc = U.to_np(eig3.eigvals(S.A.to(dev()), precision="f32c"))
+    err, tol, _ = U.check_eig_f32c(lc, S.A.double().numpy(), 1.0, SYM)
+    assert np.all(err <= tol)
+
+
+def test_scaled_identity_and_zero(eig3):
+    alphas = [0.0, 1.0, -0.1, 7.0, 3.7e-200, 1e300, -2.5e-30]
+    A = np.zeros((len(alphas), 9))
+    for i, a in enumerate(alphas):
+        A[i, [0, 4, 8]] = a
+    inv = U.to_np(eig3.invariants(torch.as_tensor(A, device=dev())))
+    assert np.all(inv[:, 1:] == 0.0)          # J2 = J3 = Delta = 0 exactly (Section J2 remark)
+    lam = U.to_np(eig3.eigvals(torch.as_tensor(A, device=dev())))
+    al = np.array(alphas)[:, None]
+    assert np.all(np.abs(lam - al) <= 2 * np.spacing(np.abs(al)))
+    A32 = torch.as_tensor(A[[0, 1, 2, 3, 6]], device=dev()).float()
+    for prec in ("f64", "f32c"):
+        lam32 = U.to_np(eig3.eigvals(A32, precision=prec))
+        a32 = A32[:, 0:1].double().cpu().numpy()
+        assert np.all(np.abs(lam32 - a32) <= 2 * np.spacing(np.abs(a32).astype(np.float32)))
+        inv32 = U.to_np(eig3.invariants(A32, precision=prec))
+        assert np.all(inv32[:, 1:] == 0.0)
+
+
+def test_diagonal_special_cases(eig3):
+    A = np.stack([np.diag([1.0, 2.0, 3.0]).reshape(9), np.diag([3.0, -1.0, 2.0]).reshape(9),
+                  np.diag([1.0, 1.0, 1.0 + 1e-8]).reshape(9)])
+    inv = U.to_np(eig3.invariants(torch.as_tensor(A, device=dev())))
+    assert inv[0, 2] == 0.0 and inv[0, 3] == 4.0     # J3 = 0, Delta = (d0 d1 d2)^2
+    assert inv[2, 3] == 0.0                          # exact double eigenvalue
+    lam = U.to_np(eig3.eigvals(torch.as_tensor(A, device=dev())))
+    ref = np.sort(np.diagonal(A.reshape(-1, 3, 3), axis1=1, axis2=2), axis=1)
+    assert np.all(np.abs(lam - ref) <= 8 * U.U64 * 3)
+
+
+def test_nonfinite_inputs_give_nan_not_trap(eig3):
+    A = np.tile(np.eye(3).reshape(1, 9), (6, 1))
+    A[0, 1] = np.nan
+    A[1, 4] = np.inf
+    A[2, 0] = -np.inf
+    st = eig3.Stats(dev())
+    lam = U.to_np(eig3.eigvals(torch.as_tensor(A, device=dev()), stats=st))
+    assert np.all(~np.isfinite(lam[:3]).all(axis=1))
+    assert np.all(np.abs(lam[3:] - 1.0) <= 4 * U.U64)
+    s = st.read()
+    assert s["n_nonfinite"] == 3
+    A32 = torch.as_tensor(A, device=dev()).float()
+    lam32 = U.to_np(eig3.eigvals(A32, precision="f32c"))
+    assert np.all(~np.isfinite(lam32[:3]).all(axis=1))
+    torch.cuda.synchronize()   # the context is still healthy
+    assert bool(torch.isfinite(eig3.eigvals(torch.eye(3, device=dev(), dtype=torch.float64)
+                                            .reshape(1, 9))).all())
+
+
+@pytest.mark.parametrize("expo", [-30, -12, 12, 30])
+def test_extreme_scales_f32c(eig3, expo):
+    S = W.workload3(n=20_000, device="cpu", seed=1700 + expo)
+    A = (S.A.double() * 10.0 ** (expo - np.log10(np.abs(S.A.double().numpy()).max()))).float()
+    lam = U.to_np(eig3.eigvals(A.to(dev()), precision="f32c"))
+    err, tol, ulps = U.check_eig_f32c(lam, A.double().numpy(), 1.0, SYM)
+    print(f"[edge] f32c scale 1e{expo}: max ulp {ulps.max():.2f}")
+    assert np.all(err <= tol)
+
+
+@pytest.mark.parametrize("expo", [-30, 30])
+def test_large_and_small_scales_f64(eig3, expo):
+    """Within the oracle's exponent range (its Delta, of degree 6, neither
+    under- nor overflows) the results match it."""
+    bt = W.workload2(n=20_000, device="cpu", seed=1800)
+    A = bt.A.numpy() * 10.0 ** expo
+    lam = U.to_np(eig3.eigvals(torch.as_tensor(A, device=dev())))
+    err, tol, bad = U.check_eig_f64(lam, A, bt.kappa.numpy(), GEN)
+    assert not bad.any()
+
+
+@pytest.mark.parametrize("k", [-900, -170, -60, 60, 170, 900])
+def test_power_of_two_scale_equivariance_f64(eig3, k):
+    """Beyond the oracle's range (Delta of a literal evaluation under- or
+    overflows once ||dev A|| leaves about [1e-51, 1e51]) the library scales the
+    deviatoric data by powers of two, which makes it exactly equivariant:
+    lambda(2^k A) = 2^k lambda(A) bit for bit, and likewise the gradient is
+    scale invariant.  The unit-scale results are pinned to the oracle above."""
+    bt = W.workload2(n=30_000, device="cpu", seed=1801)
+    A = torch.as_tensor(bt.A.numpy(), device=dev())
+    A = A[(A.abs().amax(dim=1) > 2.0 ** -60)]      # keep 2^k A free of subnormals
+    lam0, aux0 = eig3.eigvals(A, return_aux=True)
+    lamk, auxk = eig3.eigvals(A * 2.0 ** k, return_aux=True)
+    assert torch.equal(lamk, lam0 * 2.0 ** k)
+    g = torch.randn(A.shape[0], 3, dtype=torch.float64, device=dev())
+    G0 = eig3.eigvals_backward(A, g, aux=aux0)
+    Gk = eig3.eigvals_backward(A * 2.0 ** k, g, aux=auxk)
+    assert torch.equal(G0, Gk)
+    for lay, X in (("sym6", W.workload1("cpu")["sym6"].A),):
+        X = torch.as_tensor(X.numpy(), device=dev())
+        assert torch.equal(eig3.eigvals(X * 2.0 ** k), eig3.eigvals(X) * 2.0 ** k)
+
+
+@pytest.mark.parametrize("k", [-100, -40, 40, 100])
+def test_power_of_two_scale_equivariance_f32c(eig3, k):
+    S = W.workload3(n=30_000, device="cpu", seed=1802).A
+    S = torch.as_tensor(S.numpy(), device=dev())
+    big = S.abs().amax(dim=1)
+    keep = (big * 2.0 ** k < 2.0 ** 120) & (S.abs().amin(dim=1) * 2.0 ** k > 2.0 ** -120) & \
+        (S.abs().amin(dim=1) > 0)
+    S = S[keep]
+    lam0, aux0 = eig3.eigvals(S, precision="f32c", return_aux=True)
+    lamk = eig3.eigvals(S * 2.0 ** k, precision="f32c")
+    # exact equivariance needs every result (and r) to stay out of the binary32
+    # subnormal range at both scales
+    tiny = 2.0 ** -125
+    ok = (lam0.abs().amin(dim=1) * min(1.0, 2.0 ** k) > tiny) & \
+        (aux0[:, 0] * min(1.0, 2.0 ** k) > tiny)
+    assert int(ok.sum()) > 10_000
+    assert torch.equal(lamk[ok], lam0[ok] * 2.0 ** k)
+
+
+def test_misaligned_pointer_rejected(eig3):
+    """A device pointer off its element alignment is refused on the host
+    (EIG3_ERR_ALIGN) before anything is launched."""
+    buf = torch.zeros(9 * 4 + 2, dtype=torch.float32, device=dev())
+    out = torch.zeros(16, dtype=torch.float64, device=dev())
+    lib = eig3.load()
+    base = buf.data_ptr()
+    st = lib.eig3_eigvals(ctypes.c_void_p(base + 4), 0, 0, 0, 4, ctypes.c_void_p(out.data_ptr()),
+                          None, None, None)
+    assert st == 4
+    st = lib.eig3_eigvals(ctypes.c_void_p(base + 2), 0, 1, 1, 4, ctypes.c_void_p(out.data_ptr()),
+                          None, None, None)
+    assert st == 4
+    torch.cuda.synchronize()
+
+
+def test_guard_bands_untouched(eig3):
+    n = 1001
+    bt = W.workload2(n=n, device="cpu", seed=1900)
+    A = bt.A.to(dev())
+    canary = -12345.678
+    for prec, dt in (("f64", torch.float64), ("f32c", torch.float32)):
+        X = A.to(dt)
+        lam_buf = torch.full((n + 64, 3), canary, dtype=dt, device=dev())
+        aux_buf = torch.full((n + 64, 4), canary, dtype=dt, device=dev())
+        eig3.eigvals(X, precision=prec, return_aux=True, out=lam_buf[32:32 + n],
+                     aux_out=aux_buf[32:32 + n])
+        g_buf = torch.full((n + 64, 9), canary, dtype=dt, device=dev())
+        eig3.eigvals_backward(X, torch.ones(n, 3, dtype=dt, device=dev()),
+                              aux=aux_buf[32:32 + n], precision=prec, out=g_buf[32:32 + n])
+        for b in (lam_buf, aux_buf, g_buf):
+            assert bool((b[:32] == canary).all()) and bool((b[32 + n:] == canary).all())
+            assert bool((b[32:32 + n] != canary).any())
+
+
+def test_stats_struct(eig3):
+    bt = W.workload2(n=200_000, device="cpu", seed=2000)
+    A = bt.A.to(dev())
+    st = eig3.Stats(dev())
+    lam = eig3.eigvals(A, stats=st)
+    inv = eig3.invariants(A)
+    s = st.read()
+    invn = U.to_np(inv)
+    assert s["n_delta_clamped"] == int((invn[:, 3] < 0).sum())
+    assert s["n_j2_clamped"] == int((invn[:, 1] < 0).sum())
+    assert s["n_nonfinite"] == 0
+    assert s["max_abs_lambda"] == float(lam.abs().max())
+    J2 = np.maximum(invn[:, 1], 0)
+    ratio = np.maximum(invn[:, 3], 0)[J2 > 0] / J2[J2 > 0] ** 3
+    # binary32 diagnostic from the angle: relative accuracy of a few binary32 ulps
+    assert abs(s["min_disc_ratio"] - ratio.min()) <= 1e-5 * ratio.min() + 1e-30
+    assert s["n_delta_clamped"] > 0          # the near-double cases of this workload
+
+
+def test_cuda_graph_mixed_step(eig3):
+    """A small copy of the mixed workload: forward + backward on a symmetric
+    FP32 (compensated) half and a general FP64 half, captured once and
+    replayed; replays reproduce the eager results bit for bit."""
+    w5 = W.workload5(n=1 << 16, device=dev())
+    S, G = w5["sym6"], w5["general9"]
+    lamS = torch.empty(S.n, 3, dtype=torch.float32, device=dev())
+    auxS = torch.empty(S.n, 4, dtype=torch.float32, device=dev())
+    gS = torch.empty_like(S.A)
+    lamG = torch.empty(G.n, 3, dtype=torch.float64, device=dev())
+    auxG = torch.empty(G.n, 4, dtype=torch.float64, device=dev())
+    gG = torch.empty_like(G.A)
+    st = eig3.Stats(dev())
+
+    def step():
+        eig3.eigvals(S.A, precision="f32c", return_aux=True, out=lamS, aux_out=auxS, stats=st)
+        eig3.eigvals_backward(S.A, S.extra["w"], aux=auxS, precision="f32c", out=gS)
+        eig3.eigvals(G.A, precision="f64", return_aux=True, out=lamG, aux_out=auxG, stats=st)
+        eig3.eigvals_backward(G.A, G.extra["w"], aux=auxG, precision="f64", out=gG)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(s)
+    eager = [t.clone() for t in (lamS, gS, lamG, gG)]
+    for t in (lamS, gS, lamG, gG):
+        t.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(2):
+            step()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, (lamS, gS, lamG, gG)):
+        assert torch.equal(a, b)
+    # the graph's results are the library's results: check them against the oracle
+    err, tol, bad = U.check_eig_f64(U.to_np(lamG), U.to_np(G.A), U.to_np(G.kappa), GEN)
+    assert not bad.any()
+    err, tol, _ = U.check_eig_f32c(U.to_np(lamS), U.to_np(S.A), 1.0, SYM)
+    assert np.all(err <= tol)
