@@ -42,15 +42,27 @@ WORKLOAD = ("mixed fwd+bwd, 2^28 matrices/GPU: 2^27 symmetric 6-entry FP32 (comp
             "path) + 2^27 general 9-entry FP64 (FP64 path), scales 10^U[-8,8], 30% "
             "triple-perturbed, one CUDA graph per step")
 
-# Binary64 operations per matrix executed by the general 9-entry binary64
-# forward kernel (eigenvalues + adjoint inputs), counted by ncu
-# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on.sum / n).
-FWD_F64_GEN_DFMA = 128
-FWD_F64_GEN_DMUL = 46
-FWD_F64_GEN_DADD = 40
-FWD_F64_GEN_FLOP = 2 * FWD_F64_GEN_DFMA + FWD_F64_GEN_DMUL + FWD_F64_GEN_DADD
-# Peak binary64 rate from the unit counts: 152 SMs x 2 FP64 FMA lanes x 2 flop x clock.
+# Per-matrix counts of the binary64 general 9-entry forward kernel with
+# adjoint outputs and statistics (the launch of the timed step), taken with ncu
+# on n = 2^22 (bench.py --only fwd_f64_general9): thread-level instructions on
+# the FP64 pipe, of which DFMA / DMUL / DADD, and DRAM bytes read + written.
+# They describe the kernel source whose hash is recorded here; when the source
+# changes they are reported as stale and the traffic as null.
+FWD_F64_COUNTERS = {
+    "source_md5": "7d0a2c13b0cdbe16ae649d5f474e031e",
+    "fp64_pipe_inst": 196.11, "dfma": 89.0, "dmul": 73.0, "dadd": 19.0,
+    "dram_bytes": (302.071296e6 + 194.999296e6) / 4194304,
+}
+FWD_F64_SOURCES = ("eig3_f64.cuh", "eig3_f64.cu", "eig3_stats.cuh")
+# FP64 pipe of GB300: 2 FMA lanes per SM (measured with a DFMA loop: 0.598 T
+# DFMA/s at 1.97 GHz on 152 SMs), so the peak is SMs x 2 x clock instructions/s.
 FP64_LANES_PER_SM = 2
+
+
+def kernel_source_md5(names):
+    import hashlib
+    d = os.path.join(ROOT, "paper_2511_00292_gb300", "csrc")
+    return hashlib.md5(b"".join(open(os.path.join(d, f), "rb").read() for f in names)).hexdigest()
 
 
 def env_int(name, default):
@@ -58,6 +70,26 @@ def env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of a rank's shard: every rank processes its own matrices."""
+    return base + 7919 * rank
+
+
+def max_over_ranks(value: float, device) -> float:
+    """Max of a per-rank timing over the process group (identity without one)."""
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, per_rank_units: int, ms: float) -> float:
+    """Whole-job throughput in G units/s from the max-over-ranks step time."""
+    return world * per_rank_units / (ms * 1e-3) / 1e9
 
 
 def peaks():
@@ -231,7 +263,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     # ---- the mixed workload (inputs resident in HBM) ----
-    w5 = W.workload5(n=N_MIXED, device=dev, seed=1005 + 7919 * rank)
+    w5 = W.workload5(n=N_MIXED, device=dev, seed=rank_seed(1005, rank))
     S, G = w5["sym6"], w5["general9"]
     nS, nG = S.n, G.n
     lamS = torch.empty(nS, 3, dtype=torch.float32, device=dev)
@@ -289,11 +321,8 @@ def run_ours(args):
         ev1.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
     barrier()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N_MIXED / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(ms, dev)
+    value = weak_scaling_value(world, N_MIXED, ms)
 
     # ---- per-kernel durations (eager, same launches, events on the launch stream) ----
     kern = {}
@@ -303,19 +332,28 @@ def run_ours(args):
         kern[name] = timed(fn, args.steps, stream)
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = torch.cuda.get_device_properties(dev).multi_processor_count * \
-        FP64_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_inst = sms * FP64_LANES_PER_SM * sm_max * 1e6 / 1e12      # T inst/s
+    c = FWD_F64_COUNTERS
+    fresh = kernel_source_md5(FWD_F64_SOURCES) == c["source_md5"]
     t_fwdG = kern["fwd_f64_general9"] * 1e-3
-    achieved = FWD_F64_GEN_FLOP * nG / t_fwdG / 1e12
-    roofline = {"kernel": "k_eigvals<general9, f64, aux, stats> (binary64 forward)",
-                "bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops,
-                "traffic": None,
-                "peak_source": f"FP64 pipe from unit counts and clock: SMs x {FP64_LANES_PER_SM} "
-                               f"FMA/clk x 2 flop x {sm_max:.0f} MHz",
-                "algorithmic_flop_per_matrix": FWD_F64_GEN_FLOP,
-                "hbm_gbs_same_kernel": (72 + 24 + 32) * nG / t_fwdG / 1e9,
-                "hbm_peak_gbs": pk.get("hbm_gbs"), "hbm_peak_source": pk_src,
+    achieved = c["fp64_pipe_inst"] * nG / t_fwdG / 1e12
+    flop = 2 * c["dfma"] + c["dmul"] + c["dadd"]
+    roofline = {"kernel": "k_eigvals<general9, f64, aux, stats> (binary64 forward, 2^27 matrices)",
+                "bound": "alu", "unit": "T FP64-pipe inst/s", "achieved": achieved,
+                "peak": peak_inst, "frac": achieved / peak_inst,
+                "traffic": c["dram_bytes"] * nG if fresh else None,
+                "counters_fresh": fresh,
+                "peak_source": f"{sms} SMs x {FP64_LANES_PER_SM} FP64 lanes x {sm_max:.0f} MHz "
+                               f"(unit counts and clock; MEASURED_PEAKS has no FP64 figure)",
+                "algorithmic_per_matrix": {"fp64_pipe_inst": c["fp64_pipe_inst"], "dfma": c["dfma"],
+                                           "dmul": c["dmul"], "dadd": c["dadd"],
+                                           "hbm_bytes": 72 + 24 + 32},
+                "flop_view": {"achieved_tflops": flop * nG / t_fwdG / 1e12,
+                              "peak_tflops": 2 * peak_inst, "frac": flop * nG / t_fwdG / 1e12 /
+                              (2 * peak_inst)},
+                "hbm_view": {"achieved_gbs": (72 + 24 + 32) * nG / t_fwdG / 1e9,
+                             "peak_gbs": pk.get("hbm_gbs"), "peak_source": pk_src},
                 "kernel_ms": kern}
 
     # ---- the other workloads' paths (fwd, fwd+bwd, FP64 vs compensated FP32) ----
@@ -324,7 +362,7 @@ def run_ours(args):
         paths = measure_paths(eig3, W, dev, stream, args.steps)
 
     # ---- end to end through host buffers (pinned), public API ----
-    e2e = measure_e2e(eig3, S, G, dev, stream, args.steps)
+    e2e = None if args.skip_e2e else measure_e2e(eig3, S, G, dev, stream, args.steps)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -382,9 +420,16 @@ def measure_paths(eig3, W, dev, stream, steps):
 
 
 def measure_e2e(eig3, S, G, dev, stream, steps):
-    """Same step through host buffers: H2D of the inputs (matrices and loss
-    weights) from pinned memory, the four library calls, D2H of eigenvalues
-    and gradients, all inside the timed region."""
+    """The same step through host buffers (the public API on pinned host
+    tensors), every transfer inside the timed region:
+
+    zero_copy  the kernels read the matrices and loss weights straight from
+               pinned host memory and write eigenvalues and gradients straight
+               back over the host link (no staging copies; the adjoint inputs
+               stay in HBM);
+    staged     host-to-device copies of the inputs, the step on device
+               buffers, device-to-host copies of the results, one stream.
+    """
     hS = S.A.cpu().pin_memory()
     hG = G.A.cpu().pin_memory()
     hwS = S.extra["w"].cpu().pin_memory()
@@ -393,32 +438,49 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
     olG = torch.empty(G.n, 3, dtype=torch.float64).pin_memory()
     ogS = torch.empty_like(hS).pin_memory()
     ogG = torch.empty_like(hG).pin_memory()
+    auxS = torch.empty(S.n, 4, dtype=torch.float32, device=dev)
+    auxG = torch.empty(G.n, 4, dtype=torch.float64, device=dev)
+    h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
+    d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
+
+    def zero_copy_step():
+        eig3.eigvals(hS, precision="f32c", return_aux=True, out=olS, aux_out=auxS, device=dev)
+        eig3.eigvals_backward(hS, hwS, aux=auxS, precision="f32c", out=ogS, device=dev)
+        eig3.eigvals(hG, precision="f64", return_aux=True, out=olG, aux_out=auxG, device=dev)
+        eig3.eigvals_backward(hG, hwG, aux=auxG, precision="f64", out=ogG, device=dev)
+
     dS, dG = torch.empty_like(S.A), torch.empty_like(G.A)
     dwS, dwG = torch.empty_like(S.extra["w"]), torch.empty_like(G.extra["w"])
+    lS = torch.empty(S.n, 3, dtype=torch.float32, device=dev)
+    lG = torch.empty(G.n, 3, dtype=torch.float64, device=dev)
+    gS, gG = torch.empty_like(dS), torch.empty_like(dG)
 
-    def e2e_step():
+    def staged_step():
         dS.copy_(hS, non_blocking=True)
         dwS.copy_(hwS, non_blocking=True)
         dG.copy_(hG, non_blocking=True)
         dwG.copy_(hwG, non_blocking=True)
-        lS, aS = eig3.eigvals(dS, precision="f32c", return_aux=True)
-        gS = eig3.eigvals_backward(dS, dwS, aux=aS, precision="f32c")
-        lG, aG = eig3.eigvals(dG, precision="f64", return_aux=True)
-        gG = eig3.eigvals_backward(dG, dwG, aux=aG, precision="f64")
+        eig3.eigvals(dS, precision="f32c", return_aux=True, out=lS, aux_out=auxS)
+        eig3.eigvals_backward(dS, dwS, aux=auxS, precision="f32c", out=gS)
+        eig3.eigvals(dG, precision="f64", return_aux=True, out=lG, aux_out=auxG)
+        eig3.eigvals_backward(dG, dwG, aux=auxG, precision="f64", out=gG)
         olS.copy_(lS, non_blocking=True)
         ogS.copy_(gS, non_blocking=True)
         olG.copy_(lG, non_blocking=True)
         ogG.copy_(gG, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize(dev)
     k = max(1, min(steps, 3))
-    ms = timed(e2e_step, k, stream)
-    h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
-    d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
-    del hS, hG, hwS, hwG, olS, olG, ogS, ogG, dS, dG, dwS, dwG
-    return {"value": (S.n + G.n) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k}
+    out = {}
+    for name, fn in (("zero_copy", zero_copy_step), ("staged", staged_step)):
+        fn()
+        torch.cuda.synchronize(dev)
+        ms = timed(fn, k, stream)
+        out[name] = {"value": (S.n + G.n) / (ms * 1e-3) / 1e9, "ms_per_step": ms}
+    del hS, hG, hwS, hwG, olS, olG, ogS, ogG, dS, dG, dwS, dwG, lS, lG, gS, gG, auxS, auxG
+    best = "zero_copy"
+    return {"value": out[best]["value"], "unit": UNIT, "ms_per_step": out[best]["ms_per_step"],
+            "mode": best, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
+            "staged": out["staged"]}
 
 
 def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
@@ -500,6 +562,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-paths", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--only", choices=KERNELS, default=None,
                     help="time one kernel alone at size --n (profiler captures)")
     ap.add_argument("--n", type=int, default=1 << 22)

@@ -10,9 +10,12 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - All array arguments are DEVICE pointers (memory of the current CUDA
- *    device, e.g. from cudaMalloc or a torch CUDA tensor).  The caller owns
- *    every buffer; the library never allocates, frees or synchronises.
+ *  - All array arguments are pointers the current CUDA device can access:
+ *    device memory (cudaMalloc, a torch CUDA tensor), or page-locked host
+ *    memory (cudaHostAlloc / cudaHostRegister), which the kernels then read
+ *    and write directly over the host link, with no staging copy.  Pageable
+ *    host memory is not allowed.  The caller owns every buffer; the library
+ *    never allocates, frees or synchronises.
  *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
  *    NULL means the legacy default stream).  The returned status covers the
  *    host-side argument checks and the launch (cudaGetLastError); errors of

@@ -4,7 +4,8 @@ GB300 (sm_103a), after Habera & Zilian, arXiv 2511.00292.
 Every step of the computation runs in the CUDA library ``libeig3.so``
 (include/eig3.h); this module only allocates outputs with torch and passes
 pointers and the current CUDA stream.  There is no CPU path: inputs must be
-CUDA tensors and the library must be built.
+CUDA tensors, or page-locked (pinned) host tensors that the kernels read and
+write directly over the host link (zero copy), and the library must be built.
 
 Layouts: ``"general9"`` (n, 9) row-major, or (n, 3, 3); ``"sym6"`` (n, 6) in
 the order (A00, A11, A22, A12, A02, A01).
@@ -43,8 +44,9 @@ def layout_of(A: torch.Tensor, layout=None) -> int:
 
 def _rows(A: torch.Tensor, layout: int) -> torch.Tensor:
     w = 9 if layout == GENERAL9 else 6
-    if not A.is_cuda:
-        raise ValueError("eig3 runs on CUDA tensors only (no CPU path)")
+    if not A.is_cuda and not A.is_pinned():
+        raise ValueError("eig3 runs on the GPU: pass a CUDA tensor, or a page-locked (pinned) "
+                         "host tensor that the kernels read directly; there is no CPU path")
     if A.dtype not in (torch.float64, torch.float32):
         raise TypeError(f"unsupported dtype {A.dtype}; use float64 or float32")
     if not A.is_contiguous():
@@ -60,6 +62,24 @@ def _dtype_code(t: torch.Tensor) -> int:
 
 def _stream(dev: torch.device) -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _device(X: torch.Tensor, device=None) -> torch.device:
+    """The GPU that runs the kernels: the tensor's own, or for pinned host
+    tensors `device` (default: the current CUDA device)."""
+    if X.is_cuda:
+        return X.device
+    if device is not None:
+        return torch.device(device)
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def _alloc(shape, dtype, like: torch.Tensor, dev: torch.device) -> torch.Tensor:
+    """Outputs live where the input lives: on the GPU, or in pinned host memory
+    (written by the kernels over the host link) for pinned host inputs."""
+    if like.is_cuda:
+        return torch.empty(shape, dtype=dtype, device=dev)
+    return torch.empty(shape, dtype=dtype, pin_memory=True)
 
 
 def _ptr(t):
@@ -85,57 +105,62 @@ class Stats:
         return {f: getattr(s, f) for f, _ in Eig3Stats._fields_}
 
 
-def invariants(A: torch.Tensor, layout=None, precision="f64") -> torch.Tensor:
+def invariants(A: torch.Tensor, layout=None, precision="f64", device=None) -> torch.Tensor:
     """(n, 4) float64 tensor of (I1, J2, J3, Delta) (Algorithms 1, 2, 4, 5)."""
     lay = layout_of(A, layout)
     X = _rows(A, lay)
-    out = torch.empty((X.shape[0], 4), dtype=torch.float64, device=X.device)
-    with torch.cuda.device(X.device):
+    dev = _device(X, device)
+    out = _alloc((X.shape[0], 4), torch.float64, X, dev)
+    with torch.cuda.device(dev):
         st = load().eig3_invariants(_ptr(X), lay, _dtype_code(X), _PRECS[precision], X.shape[0],
-                                    _ptr(out), _stream(X.device))
+                                    _ptr(out), _stream(dev))
     check(st, "eig3_invariants")
     return out
 
 
 def eigvals(A: torch.Tensor, layout=None, precision="f64", return_aux=False, stats=None,
-            out=None, aux_out=None):
+            out=None, aux_out=None, device=None):
     """Ascending eigenvalues, (n, 3) in the storage dtype (Algorithm 6).
 
     With ``return_aux`` also returns the (n, 4) adjoint inputs
     (r, sin(phi/3), sin((pi-phi)/3), I1) for :func:`eigvals_backward`.
     ``out`` / ``aux_out`` may supply preallocated outputs (CUDA-graph use).
+    A pinned host ``A`` is read by the kernels directly (zero copy); the
+    eigenvalues then go to pinned host memory and ``aux`` to the GPU.
     """
     lay = layout_of(A, layout)
     X = _rows(A, lay)
     n = X.shape[0]
-    lam = out if out is not None else torch.empty((n, 3), dtype=X.dtype, device=X.device)
+    dev = _device(X, device)
+    lam = out if out is not None else _alloc((n, 3), X.dtype, X, dev)
     aux = None
     if return_aux:
-        aux = aux_out if aux_out is not None else torch.empty((n, 4), dtype=X.dtype,
-                                                              device=X.device)
+        aux = aux_out if aux_out is not None else torch.empty((n, 4), dtype=X.dtype, device=dev)
     sp = _ptr(stats.buf) if stats is not None else None
-    with torch.cuda.device(X.device):
+    with torch.cuda.device(dev):
         st = load().eig3_eigvals(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n, _ptr(lam),
-                                 _ptr(aux), sp, _stream(X.device))
+                                 _ptr(aux), sp, _stream(dev))
     check(st, "eig3_eigvals")
     return (lam, aux) if return_aux else lam
 
 
 def eigvals_backward(A: torch.Tensor, grad_lam: torch.Tensor, aux=None, layout=None,
-                     precision="f64", out=None) -> torch.Tensor:
-    """dL/dA (same shape and dtype as the stored rows) given dL/dlambda (n, 3)."""
+                     precision="f64", out=None, device=None) -> torch.Tensor:
+    """dL/dA (same shape and dtype as the stored rows) given dL/dlambda (n, 3).
+    Pinned host ``A`` / ``grad_lam`` are read directly by the kernels."""
     lay = layout_of(A, layout)
     X = _rows(A, lay)
-    g = grad_lam.contiguous()
-    if g.dtype != X.dtype or g.numel() != 3 * X.shape[0] or not g.is_cuda:
-        raise ValueError("grad_lam must be a CUDA (n, 3) tensor of the storage dtype")
+    g = grad_lam if grad_lam.is_contiguous() else grad_lam.contiguous()
+    if g.dtype != X.dtype or g.numel() != 3 * X.shape[0] or not (g.is_cuda or g.is_pinned()):
+        raise ValueError("grad_lam must be a CUDA or pinned (n, 3) tensor of the storage dtype")
     if aux is not None and (aux.dtype != X.dtype or aux.numel() != 4 * X.shape[0]):
         raise ValueError("aux must be the (n, 4) tensor returned by eigvals(return_aux=True)")
-    gA = out if out is not None else torch.empty_like(X)
-    with torch.cuda.device(X.device):
+    dev = _device(X, device)
+    gA = out if out is not None else _alloc(tuple(X.shape), X.dtype, X, dev)
+    with torch.cuda.device(dev):
         st = load().eig3_eigvals_backward(_ptr(X), lay, _dtype_code(X), _PRECS[precision],
                                           X.shape[0], _ptr(g), _ptr(aux), _ptr(gA),
-                                          _stream(X.device))
+                                          _stream(dev))
     check(st, "eig3_eigvals_backward")
     return gA
 

@@ -47,6 +47,16 @@ __device__ __forceinline__ double pow2d(int k) {  // 2^k for -1022 <= k <= 1023
   return __hiloint2double((k + 1023) << 20, 0);
 }
 
+// max(x, 0) by the sign bit (integer pipe, not the FP64 pipe); -0 and NaNs
+// with the sign bit set give +0, like fmax(x, 0).
+__device__ __forceinline__ double nonneg(double x) { return __double2hiint(x) < 0 ? 0.0 : x; }
+
+// x < 0 (excluding -0) by the bits.
+__device__ __forceinline__ bool negative(double x) {
+  const int hi = __double2hiint(x);
+  return hi < 0 && ((hi & 0x7fffffff) | __double2loint(x)) != 0;
+}
+
 template <int N>
 __device__ __forceinline__ int dev_scale(double (&v)[N]) {
   int h = hi_abs(v[0]);
@@ -242,33 +252,33 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   const int e = min((h >> 20) & 0x7ff, 2045);
   const double sc = __hiloint2double((2046 - e) << 20, 0);
   const double X = ax * sc, Y = y * sc;
-  // binary32 seed
+  // binary32 seed w0 = c0 + i s0
   const float pf = atan2f(__double2float_rn(Y), __double2float_rn(X)) * (1.0f / 3.0f);
   float sf, cf;
   __sincosf(pf, &sf, &cf);
   const double c0 = (double)cf, s0 = (double)sf;
-  // w0^3
-  const double a2 = fma(c0, c0, -(s0 * s0));
-  const double b2 = (c0 + c0) * s0;
-  const double a3 = fma(a2, c0, -(b2 * s0));
-  const double b3 = fma(a2, s0, b2 * c0);
-  // rho = z conj(w0^3); its argument is 3 eps
+  const double cc = c0 * c0, ss = s0 * s0;  // exact: 24-bit factors
+  // w0^3 = c0 (c0^2 - 3 s0^2) + i s0 (3 c0^2 - s0^2)
+  const double a3 = c0 * fma(-3.0, ss, cc);
+  const double b3 = s0 * fma(3.0, cc, -ss);
+  // rho = z conj(w0^3); its argument is 3 eps (|3 eps| ~ 1e-6: arg = Im/Re to 1e-18)
   const double re = fma(X, a3, Y * b3);
   const double im = fma(Y, a3, -(X * b3));
   const double rc0 = (double)__frcp_rn(__double2float_rn(re));
   const double rc = fma(rc0, fma(-re, rc0, 1.0), rc0);
-  double eps = (im * rc) * kInv3;
-  eps = (re > 0.0) ? eps : 0.0;  // z = 0: the angle is undetermined, keep phi = 0
-  // w1 = w0 e^{i eps}, then |w1| -> 1
-  const double ce = fma(-0.5 * eps, eps, 1.0);
-  const double c1 = fma(c0, ce, -(s0 * eps));
-  const double s1 = fma(s0, ce, c0 * eps);
-  const double eta = fma(c1, c1, s1 * s1) - 1.0;
-  const double f = fma(eta, fma(eta, 0.375, -0.5), 1.0);
-  const double ct = c1 * f;
-  const double st = fmax(s1 * f, 0.0);
+  // z = 0 (re = +0): the angle is undetermined, keep phi = 0
+  const double eps = (__double2hiint(re) > 0) ? (im * rc) * kInv3 : 0.0;
+  // 1/|w0| to second order in eta0 = |w0|^2 - 1 (|eta0| ~ 1e-7), folded into
+  // the rotation w~ = w0 e^{i eps} / |w0| with e^{i eps} = 1 - eps^2/2 + i eps
+  const double eta0 = (cc - 1.0) + ss;
+  const double f0 = fma(eta0, fma(eta0, 0.375, -0.5), 1.0);
+  const double ef = f0 * eps;
+  const double cef = fma(-0.5 * eps, ef, f0);
+  const double ct = fma(c0, cef, -(s0 * ef));
+  const double st = nonneg(fma(s0, cef, c0 * ef));
   const double other = fma(kHalfSqrt3, ct, -0.5 * st);  // sin(pi/3 - psi~)
-  const bool pos = !(x < 0.0);
+  // sign test on the bits: x = -0 goes with x < 0, as atan2(0, -0) = pi does
+  const bool pos = __double2hiint(x) >= 0;
   sigma1 = pos ? st : other;
   sigma2 = pos ? other : st;
 }
@@ -288,10 +298,10 @@ struct Eig {
 
 __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
   Eig o;
-  o.j2_clamped = v.J2 < 0.0;
-  o.d_clamped = v.D < 0.0;
-  const double J2p = fmax(v.J2, 0.0);
-  const double Dp = fmax(v.D, 0.0);
+  o.j2_clamped = negative(v.J2);
+  o.d_clamped = negative(v.D);
+  const double J2p = nonneg(v.J2);
+  const double Dp = nonneg(v.D);
   o.r = sqrt(3.0 * J2p);
   if (v.e != 0) o.r *= pow2d(v.e);
   triple_angle_sines(27.0 * v.J3, sqrt(27.0 * Dp), o.sigma1, o.sigma2);
@@ -333,17 +343,31 @@ struct Adj {
 
 __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double sigma2, double g1,
                                                double g2, double g3) {
-  const double g12 = kTwoOverSqrt3 * sigma1;
-  const double g23 = kTwoOverSqrt3 * sigma2;
-  const double g13 = kTwoOverSqrt3 * (sigma1 + sigma2);
-  const double D12 = (g12 != 0.0) ? (g2 - g1) / g12 : 0.0;
-  const double D23 = (g23 != 0.0) ? (g3 - g2) / g23 : 0.0;
+  // Sigmas below 2^-960 count as exact coalescence (divided difference 0).
+  const bool z1 = hi_abs(sigma1) < (63 << 20);
+  const bool z2 = hi_abs(sigma2) < (63 << 20);
+  const double s1 = z1 ? 1.0 : sigma1, s2 = z2 ? 1.0 : sigma2;
+  const double s3 = sigma1 + sigma2;  // >= sin(pi/6) cos(pi/6): never 0
+  // One division serves all four reciprocals: with r = m 2^k, m in [1, 4),
+  // and P = s1 s2 s3,  R = 1 / (m P) gives  1/r = P R 2^-k  and
+  // (sqrt3/2)/s_i = (sqrt3/2) (P/s_i) (m R).  (The gaps in units of r are
+  // (2/sqrt3) sigma1, (2/sqrt3) sigma2 and (2/sqrt3)(sigma1 + sigma2).)
+  const int hr = hi_abs(r);
+  const bool rz = hr < (1 << 20);  // r = 0 or subnormal: a triple eigenvalue
+  const int kr = min((hr >> 20) - 1023, 1022);
+  const double p2k = pow2d(-kr);
+  const double m = rz ? 1.0 : r * p2k;
+  const double s12 = s1 * s2;
+  const double P = s12 * s3;
+  const double R = 1.0 / (m * P);
+  const double Rh = kHalfSqrt3 * (m * R);  // (sqrt3/2) / P
+  const double D12 = z1 ? 0.0 : (g2 - g1) * ((s2 * s3) * Rh);
+  const double D23 = z2 ? 0.0 : (g3 - g2) * ((s1 * s3) * Rh);
   Adj o;
-  o.aJ3r2 = (g13 != 0.0) ? (D23 - D12) / g13 : 0.0;
+  o.aJ3r2 = (D23 - D12) * (s12 * Rh);
   o.aJ2r = fma(-kK * fma(2.0, sigma1, sigma2), o.aJ3r2, D23);
   o.aI1 = ((g1 + g2) + g3) * kInv3;
-  // r below the normal range counts as a triple eigenvalue
-  o.inv_r = (r >= 2.2250738585072014e-308) ? 1.0 / r : 0.0;
+  o.inv_r = rz ? 0.0 : (P * R) * p2k;
   return o;
 }
 

@@ -256,3 +256,27 @@ def test_cuda_graph_mixed_step(eig3):
     assert not bad.any()
     err, tol, _ = U.check_eig_f32c(U.to_np(lamS), U.to_np(S.A), 1.0, SYM)
     assert np.all(err <= tol)
+
+
+def test_zero_copy_pinned_host_buffers(eig3):
+    """Kernels reading and writing page-locked host memory directly give the
+    same bits as on device-resident buffers."""
+    bt = W.workload2(n=70_001, device="cpu", seed=2100)
+    hA = bt.A.pin_memory()
+    dA = bt.A.to(dev())
+    lam_h, aux_h = eig3.eigvals(hA, return_aux=True, device=dev())
+    torch.cuda.synchronize()
+    assert not lam_h.is_cuda and lam_h.is_pinned()
+    lam_d, aux_d = eig3.eigvals(dA, return_aux=True)
+    assert torch.equal(lam_h, lam_d.cpu())
+    hw = torch.randn(bt.n, 3, dtype=torch.float64).pin_memory()
+    g_h = eig3.eigvals_backward(hA, hw, aux=aux_h, device=dev())
+    torch.cuda.synchronize()
+    g_d = eig3.eigvals_backward(dA, hw.to(dev()), aux=aux_d)
+    assert torch.equal(g_h, g_d.cpu())
+    S = W.workload3(n=50_001, device="cpu", seed=2101).A
+    l_h = eig3.eigvals(S.pin_memory(), precision="f32c", device=dev())
+    torch.cuda.synchronize()
+    assert torch.equal(l_h, eig3.eigvals(S.to(dev()), precision="f32c").cpu())
+    with pytest.raises(ValueError):
+        eig3.eigvals(bt.A)          # pageable host memory is refused
