@@ -1,12 +1,15 @@
 // eig3_f32c.cu -- compensated binary32 kernels (storage and arithmetic in
 // binary32, see eig3_f32c.cuh): invariants, eigenvalues (+ adjoint inputs,
-// + statistics) and the adjoint, for both layouts.  One thread per matrix,
-// grid-stride over the batch.
+// + statistics) and the adjoint, for both layouts.  One thread per matrix;
+// blocks walk the batch in tiles of 256 rows whose inputs are copied into
+// shared memory asynchronously, one tile ahead (eig3_tile.cuh); the 16-byte
+// adjoint-input rows move as one float4 each; outputs are stored directly.
 #include <cstdint>
 
 #include "eig3_f32c.cuh"
 #include "eig3_internal.h"
 #include "eig3_stats.cuh"
+#include "eig3_tile.cuh"
 
 namespace eig3 {
 namespace {
@@ -53,29 +56,59 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+__device__ __forceinline__ bool aligned16c(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
 template <int LAYOUT, bool AUX, bool STATS>
 __global__ void __launch_bounds__(kThreads)
     k_eigvals_c(const float *__restrict__ A, int64_t n, float *__restrict__ lam,
                 float *__restrict__ aux, eig3_stats *__restrict__ stats) {
   constexpr int N = WidthC<LAYOUT>::N;
+  __shared__ __align__(16) float sA[2][kTile * N];
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    float a[N];
-    load_f<N>(A, i, a);
-    const InvC v = invariants_c<LAYOUT, N>(a);
-    const EigC e = eigvals_c(v);
-    const float l[3] = {e.l1, e.l2, e.l3};
-    store_f<3>(lam, i, l);
-    if constexpr (AUX) {
-      const float x[4] = {e.r, e.sigma1, e.sigma2, e.I1};
-      store_f<4>(aux, i, x);
+  const bool vaux = AUX && aligned16c(aux);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles)
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kTile;
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) {
+      float a[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
+      const InvC v = invariants_c<LAYOUT, N>(a);
+      const EigC e = eigvals_c(v);
+      const int64_t i = r0 + threadIdx.x;
+      lam[3 * i + 0] = e.l1;
+      lam[3 * i + 1] = e.l2;
+      lam[3 * i + 2] = e.l3;
+      if constexpr (AUX) {
+        if (vaux) {
+          *reinterpret_cast<float4 *>(aux + 4 * i) = make_float4(e.r, e.sigma1, e.sigma2, e.I1);
+        } else {
+          aux[4 * i] = e.r;
+          aux[4 * i + 1] = e.sigma1;
+          aux[4 * i + 2] = e.sigma2;
+          aux[4 * i + 3] = e.I1;
+        }
+      }
+      if constexpr (STATS) {
+        stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0f, fminf(e.sigma1, e.sigma2), e.l1,
+                 e.l2, e.l3);
+      }
     }
-    if constexpr (STATS) {
-      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0f, fminf(e.sigma1, e.sigma2), e.l1,
-               e.l2, e.l3);
-    }
+    buf ^= 1;
   }
   if constexpr (STATS) stat_flush(acc, stats);
 }
@@ -85,33 +118,66 @@ __global__ void __launch_bounds__(kThreads)
     k_backward_c(const float *__restrict__ A, int64_t n, const float *__restrict__ g,
                  const float *__restrict__ aux, float *__restrict__ gA) {
   constexpr int N = WidthC<LAYOUT>::N;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    float a[N];
-    load_f<N>(A, i, a);
-    float gb[3];
-    load_f<3>(g, i, gb);
-    float r, s1, s2;
-    if constexpr (AUX) {
-      float x[4];
-      load_f<4>(aux, i, x);
-      r = x[0];
-      s1 = x[1];
-      s2 = x[2];
-    } else {
-      const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
-      r = e.r;
-      s1 = e.sigma1;
-      s2 = e.sigma2;
+  __shared__ __align__(16) float sA[2][kTile * N];
+  __shared__ __align__(16) float sG[2][kTile * 3];
+  const bool vaux = AUX && aligned16c(aux);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles) {
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+    tile_issue(g, (int64_t)blockIdx.x * kTile * 3, rows_of(blockIdx.x) * 3, sG[0]);
+  }
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kTile;
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) {
+      tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+      tile_issue(g, tn * kTile * 3, rows_of(tn) * 3, sG[buf ^ 1]);
     }
-    const AdjC s = adjoint_c(r, s1, s2, gb[0], gb[1], gb[2]);
-    float G[N];
-    if constexpr (LAYOUT == EIG3_GENERAL9) {
-      grad_general_c(a, s, G);
-    } else {
-      grad_sym_c(a, s, G);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) {
+      float a[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
+      const float g1 = sG[buf][threadIdx.x * 3 + 0];
+      const float g2 = sG[buf][threadIdx.x * 3 + 1];
+      const float g3 = sG[buf][threadIdx.x * 3 + 2];
+      const int64_t i = r0 + threadIdx.x;
+      float r, s1, s2;
+      if constexpr (AUX) {
+        if (vaux) {
+          const float4 x = __ldg(reinterpret_cast<const float4 *>(aux + 4 * i));
+          r = x.x;
+          s1 = x.y;
+          s2 = x.z;
+        } else {
+          r = __ldg(aux + 4 * i);
+          s1 = __ldg(aux + 4 * i + 1);
+          s2 = __ldg(aux + 4 * i + 2);
+        }
+      } else {
+        const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+        r = e.r;
+        s1 = e.sigma1;
+        s2 = e.sigma2;
+      }
+      const AdjC s = adjoint_c(r, s1, s2, g1, g2, g3);
+      float G[N];
+      if constexpr (LAYOUT == EIG3_GENERAL9) {
+        grad_general_c(a, s, G);
+      } else {
+        grad_sym_c(a, s, G);
+      }
+      float *q = gA + N * i;
+#pragma unroll
+      for (int j = 0; j < N; ++j) q[j] = G[j];
     }
-    store_f<N>(gA, i, G);
+    buf ^= 1;
   }
 }
 

@@ -86,7 +86,22 @@ __device__ __forceinline__ Sum operator+(Sum a, Sum b) {
 
 __device__ __forceinline__ F2 done(Sum a) { return two_sum(a.s, a.c); }
 
+// A Sum state is itself an unevaluated pair s + c (not normalised: after
+// cancellation |c| may approach |s|).  It enters products and squares as it
+// is; the dropped low-by-low terms stay at the working precision squared
+// relative to the summed terms, which is the accuracy of Sum2 itself.
+__device__ __forceinline__ F2 pair(Sum a) { return {a.s, a.c}; }
+
+// (s + c)^2 = s^2 + c (2 s + c), keeping the c^2 term.
+__device__ __forceinline__ F2 sq(Sum a) {
+  const float p = __fmul_rn(a.s, a.s);
+  const float e = __fmaf_rn(a.s, a.s, -p);
+  return {p, __fmaf_rn(a.c, __fmaf_rn(2.0f, a.s, a.c), e)};
+}
+
 __device__ __forceinline__ float round1(F2 x) { return __fadd_rn(x.h, x.l); }
+
+__device__ __forceinline__ float round1(Sum x) { return __fadd_rn(x.s, x.c); }
 
 // (x.h + x.l)^2 to first order, as a pair.
 __device__ __forceinline__ F2 sq(F2 x) {
@@ -95,10 +110,10 @@ __device__ __forceinline__ F2 sq(F2 x) {
   return {p, __fmaf_rn(__fadd_rn(x.h, x.h), x.l, e)};
 }
 
-// Invariants in scaled form.  With s = 2^-e the scale:
+// Invariants in scaled form (Sum2 states).  With s = 2^-e the scale:
 //   J2x6 = 6 J2 s^2, J3x27 = 27 J3 s^3, D = Delta s^6, I1 unscaled.
 struct InvC {
-  F2 I1, J2x6, J3x27, D;
+  Sum I1, J2x6, J3x27, D;
   int e;  // the scale exponent
 };
 
@@ -128,7 +143,8 @@ __device__ __forceinline__ float unscale_pow2(int e) {
 
 // Diagonal differences as exact pairs, the trace as an exact pair.
 struct Diag {
-  F2 d0, d1, d2, I1;
+  F2 d0, d1, d2;
+  Sum I1;
 };
 
 __device__ __forceinline__ Diag diag_parts(float a00, float a11, float a22) {
@@ -138,7 +154,7 @@ __device__ __forceinline__ Diag diag_parts(float a00, float a11, float a22) {
   g.d2 = two_sum(a11, -a22);
   const F2 t = two_sum(a00, a11);
   const F2 u = two_sum(t.h, a22);
-  g.I1 = two_sum(u.h, __fadd_rn(t.l, u.l));
+  g.I1 = {u.h, __fadd_rn(t.l, u.l)};
   return g;
 }
 
@@ -171,38 +187,35 @@ __device__ __forceinline__ InvC invariants_sym_c(float a00, float a11, float a22
   const F2 aa = two_prod(a, a), bb = two_prod(b, b), cc = two_prod(c, c);
   const F2 ab = two_prod(a, b), ac = two_prod(a, c), bc = two_prod(b, c);
   // Algorithm 2, times 6: (d0^2 + d1^2 + d2^2) + 6 (aa + bb + cc)
-  const F2 off = done(start(aa) + bb + cc);
-  const Sum dsq = start(sq(d0)) + sq(d1) + sq(d2);
-  o.J2x6 = done(dsq + mul(off, 6.0f));
+  const Sum off = start(aa) + bb + cc;
+  o.J2x6 = start(sq(d0)) + sq(d1) + sq(d2) + mul(pair(off), 6.0f);
   // Algorithm 4, times 27: 27 * 2abc + 9 (aa t1 + bb t2 + cc t3) - t1 t2 t3
-  const F2 t1 = done(start(d1) + d2);
-  const F2 t2 = done(start(d0) - d2);
-  const F2 t3 = done(start(neg(d0)) - d1);
+  const F2 t1 = pair(start(d1) + d2);
+  const F2 t2 = pair(start(d0) - d2);
+  const F2 t3 = pair(start(neg(d0)) - d1);
   const F2 abc = mul(ab, c);
-  const F2 mixed = done(start(mul(aa, t1)) + mul(bb, t2) + mul(cc, t3));
-  o.J3x27 = done(start(mul(abc, 54.0f)) + mul(mixed, 9.0f) - mul(mul(t1, t2), t3));
+  const Sum mixed = start(mul(aa, t1)) + mul(bb, t2) + mul(cc, t3);
+  o.J3x27 = start(mul(abc, 54.0f)) + mul(pair(mixed), 9.0f) - mul(mul(t1, t2), t3);
   // Algorithm 5
   const F2 d0d1 = mul(d0, d1), d0d2 = mul(d0, d2), d1d2 = mul(d1, d2);
   const F2 aac = mul(aa, c), bbc = mul(bb, c), aab = mul(aa, b), ccb = mul(cc, b);
   const F2 cca = mul(cc, a), bba = mul(bb, a);
-  const F2 r2 = done(start(neg(mul(ab, d2))) + aac - bbc);
-  const F2 r3 = done(start(mul(ac, d1)) - aab + ccb);
-  const F2 r4 = done(start(mul(bc, d0)) + cca - bba);
+  const Sum r2 = start(neg(mul(ab, d2))) + aac - bbc;
+  const Sum r3 = start(mul(ac, d1)) - aab + ccb;
+  const Sum r4 = start(mul(bc, d0)) + cca - bba;
   const Sum s89 = start(mul(d0d1, c)) - mul(cc, c);
-  const F2 r8 = done(s89 + aac - mul(ab, d1));
-  const F2 r9 = done(s89 + bbc - mul(ab, d0));
+  const Sum r8 = s89 + aac - mul(ab, d1);
+  const Sum r9 = s89 + bbc - mul(ab, d0);
   const Sum s1011 = start(mul(d1d2, a)) - mul(aa, a);
-  const F2 r10 = done(s1011 + mul(bc, d2) + bba);
-  const F2 r11 = done(s1011 + mul(bc, d1) + cca);
+  const Sum r10 = s1011 + mul(bc, d2) + bba;
+  const Sum r11 = s1011 + mul(bc, d1) + cca;
   const Sum s1213 = start(mul(d0d2, b)) + mul(bb, b);
-  const F2 r13 = done(s1213 + mul(ac, d2) - aab);
-  const F2 r12 = done(-s1213 + mul(ac, d0) + ccb);
-  const F2 r14 =
-      done(start(mul(d0d1, d2)) - mul(aa, d0) + mul(bb, d1) - mul(cc, d2));
-  const F2 g14 = done(start(sq(r2)) + sq(r3) + sq(r4));
+  const Sum r13 = s1213 + mul(ac, d2) - aab;
+  const Sum r12 = -s1213 + mul(ac, d0) + ccb;
+  const Sum r14 = start(mul(d0d1, d2)) - mul(aa, d0) + mul(bb, d1) - mul(cc, d2);
+  const Sum g14 = start(sq(r2)) + sq(r3) + sq(r4);
   const Sum g2 = start(sq(r8)) + sq(r9) + sq(r10) + sq(r11) + sq(r12) + sq(r13);
-  const F2 g2d = done(g2);
-  o.D = done(start(mul(g14, 14.0f)) + scale2(g2d, 2.0f) + sq(r14));
+  o.D = start(mul(pair(g14), 14.0f)) + scale2(pair(g2), 2.0f) + sq(r14);
   return o;
 }
 
@@ -216,7 +229,7 @@ struct Shared {
 };
 
 struct R13 {
-  F2 r[13];  // r1 .. r13
+  Sum r[13];  // r1 .. r13
 };
 
 __device__ __forceinline__ R13 dx_c(float M01, float M02, float M10, float M12, float M20,
@@ -228,34 +241,34 @@ __device__ __forceinline__ R13 dx_c(float M01, float M02, float M10, float M12, 
   const F2 m0221 = two_prod(M02, M21), m0212 = two_prod(M02, M12);
   const F2 m1212 = two_prod(M12, M12);
   // r1 = M01 M12 M20 - M02 M10 M21
-  o.r[0] = done(start(mul(m0112, M20)) - mul(m0210, M21));
+  o.r[0] = start(mul(m0112, M20)) - mul(m0210, M21);
   // r2 = -M01 M02 d2 + M01^2 M12 - M02^2 M21
-  o.r[1] = done(start(neg(mul(m0102, s.d2))) + mul(m0101, M12) - mul(m0202, M21));
+  o.r[1] = start(neg(mul(m0102, s.d2))) + mul(m0101, M12) - mul(m0202, M21);
   // r3 = M01 M21 d1 - M01^2 M20 + M02 M21^2
-  o.r[2] = done(start(mul(m0121, s.d1)) - mul(m0101, M20) + mul(m0221, M21));
+  o.r[2] = start(mul(m0121, s.d1)) - mul(m0101, M20) + mul(m0221, M21);
   // r4 = M02 M12 d0 + M01 M12^2 - M02^2 M10
-  o.r[3] = done(start(mul(m0212, s.d0)) + mul(m0112, M12) - mul(m0202, M10));
+  o.r[3] = start(mul(m0212, s.d0)) + mul(m0112, M12) - mul(m0202, M10);
   // r5 = M01 M12 d1 - M01 M02 M10 + M02 M12 M21
-  o.r[4] = done(start(mul(m0112, s.d1)) - mul(m0102, M10) + mul(m0212, M21));
+  o.r[4] = start(mul(m0112, s.d1)) - mul(m0102, M10) + mul(m0212, M21);
   // r6 = M02 M21 d0 - M01 M02 M20 + M01 M12 M21
-  o.r[5] = done(start(mul(m0221, s.d0)) - mul(m0102, M20) + mul(m0112, M21));
+  o.r[5] = start(mul(m0221, s.d0)) - mul(m0102, M20) + mul(m0112, M21);
   // r7 = -M02 M10 d2 + M01 M10 M12 - M02 M12 M20
-  o.r[6] = done(start(neg(mul(m0210, s.d2))) + mul(s.p01, M12) - mul(m0212, M20));
+  o.r[6] = start(neg(mul(m0210, s.d2))) + mul(s.p01, M12) - mul(m0212, M20);
   // r8 = M12 d0 d1 - M02 M10 d1 + M01 M10 M12 - M12^2 M21
   // r9 = M12 d0 d1 - M02 M10 d0 + M02 M12 M20 - M12^2 M21
   const Sum s89 = start(mul(s.d0d1, M12)) - mul(m1212, M21);
-  o.r[7] = done(s89 - mul(m0210, s.d1) + mul(s.p01, M12));
-  o.r[8] = done(s89 - mul(m0210, s.d0) + mul(m0212, M20));
+  o.r[7] = s89 - mul(m0210, s.d1) + mul(s.p01, M12);
+  o.r[8] = s89 - mul(m0210, s.d0) + mul(m0212, M20);
   // r10 = M01 d1 d2 + M02 M21 d2 + M01 M02 M20 - M01^2 M10
   // r11 = M01 d1 d2 + M02 M21 d1 + M01 M12 M21 - M01^2 M10
   const Sum s1011 = start(mul(s.d1d2, M01)) - mul(m0101, M10);
-  o.r[9] = done(s1011 + mul(m0221, s.d2) + mul(m0102, M20));
-  o.r[10] = done(s1011 + mul(m0221, s.d1) + mul(m0112, M21));
+  o.r[9] = s1011 + mul(m0221, s.d2) + mul(m0102, M20);
+  o.r[10] = s1011 + mul(m0221, s.d1) + mul(m0112, M21);
   // r12 = -M02 d0 d2 + M01 M12 d0 + M02 M12 M21 - M02^2 M20
   // r13 =  M02 d0 d2 + M01 M12 d2 - M01 M02 M10 + M02^2 M20
   const Sum s1213 = start(mul(s.d0d2, M02)) + mul(m0202, M20);
-  o.r[11] = done(-s1213 + mul(m0112, s.d0) + mul(m0212, M21));
-  o.r[12] = done(s1213 + mul(m0112, s.d2) - mul(m0102, M10));
+  o.r[11] = -s1213 + mul(m0112, s.d0) + mul(m0212, M21);
+  o.r[12] = s1213 + mul(m0112, s.d2) - mul(m0102, M10);
   return o;
 }
 
@@ -276,31 +289,32 @@ __device__ __forceinline__ InvC invariants_general_c(const float (&a)[9]) {
   s.p02 = two_prod(A02, A20);
   s.p12 = two_prod(A12, A21);
   // Algorithm 2, times 6
-  const F2 off = done(start(s.p01) + s.p02 + s.p12);
-  o.J2x6 = done(start(sq(s.d0)) + sq(s.d1) + sq(s.d2) + mul(off, 6.0f));
+  const Sum off = start(s.p01) + s.p02 + s.p12;
+  o.J2x6 = start(sq(s.d0)) + sq(s.d1) + sq(s.d2) + mul(pair(off), 6.0f);
   // Algorithm 4, times 27
-  const F2 t1 = done(start(s.d1) + s.d2);
-  const F2 t2 = done(start(s.d0) - s.d2);
-  const F2 t3 = done(start(neg(s.d0)) - s.d1);
-  const F2 offd = done(start(mul(two_prod(A01, A12), A20)) + mul(two_prod(A02, A10), A21));
-  const F2 mixed = done(start(mul(s.p01, t1)) + mul(s.p02, t2) + mul(s.p12, t3));
-  o.J3x27 = done(start(mul(offd, 27.0f)) + mul(mixed, 9.0f) - mul(mul(t1, t2), t3));
+  const F2 t1 = pair(start(s.d1) + s.d2);
+  const F2 t2 = pair(start(s.d0) - s.d2);
+  const F2 t3 = pair(start(neg(s.d0)) - s.d1);
+  const Sum offd = start(mul(two_prod(A01, A12), A20)) + mul(two_prod(A02, A10), A21);
+  const Sum mixed = start(mul(s.p01, t1)) + mul(s.p02, t2) + mul(s.p12, t3);
+  o.J3x27 = start(mul(pair(offd), 27.0f)) + mul(pair(mixed), 9.0f) - mul(mul(t1, t2), t3);
   // Algorithm 5
   s.d0d1 = mul(s.d0, s.d1);
   s.d0d2 = mul(s.d0, s.d2);
   s.d1d2 = mul(s.d1, s.d2);
   // r14 = d0 d1 d2 - M01 M10 d0 + M02 M20 d1 - M12 M21 d2 (same for A and A^T)
-  const F2 r14 =
-      done(start(mul(s.d0d1, s.d2)) - mul(s.p01, s.d0) + mul(s.p02, s.d1) - mul(s.p12, s.d2));
+  const Sum r14 =
+      start(mul(s.d0d1, s.d2)) - mul(s.p01, s.d0) + mul(s.p02, s.d1) - mul(s.p12, s.d2);
   const R13 u = dx_c(A01, A02, A10, A12, A20, A21, s);
   const R13 v = dx_c(A10, A20, A01, A21, A02, A12, s);
   // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1)
-  const F2 g6 = done(start(mul(u.r[1], v.r[1])) + mul(u.r[2], v.r[2]) + mul(u.r[3], v.r[3]));
-  const F2 g8 = done(start(mul(u.r[4], v.r[4])) + mul(u.r[5], v.r[5]) + mul(u.r[6], v.r[6]));
-  const F2 g2 = done(start(mul(u.r[7], v.r[7])) + mul(u.r[8], v.r[8]) + mul(u.r[9], v.r[9]) +
-                     mul(u.r[10], v.r[10]) + mul(u.r[11], v.r[11]) + mul(u.r[12], v.r[12]));
-  o.D = done(start(mul(mul(u.r[0], v.r[0]), 9.0f)) + mul(g6, 6.0f) + scale2(g8, 8.0f) +
-             scale2(g2, 2.0f) + sq(r14));
+#define UV(k) mul(pair(u.r[k]), pair(v.r[k]))
+  const Sum g6 = start(UV(1)) + UV(2) + UV(3);
+  const Sum g8 = start(UV(4)) + UV(5) + UV(6);
+  const Sum g2 = start(UV(7)) + UV(8) + UV(9) + UV(10) + UV(11) + UV(12);
+  o.D = start(mul(UV(0), 9.0f)) + mul(pair(g6), 6.0f) + scale2(pair(g8), 8.0f) +
+        scale2(pair(g2), 2.0f) + sq(r14);
+#undef UV
   return o;
 }
 
@@ -312,6 +326,23 @@ __device__ __forceinline__ InvC invariants_general_c(const float (&a)[9]) {
 //   lambda_1 = I1/3 - k (sigma2 + 2 sigma1), lambda_2 = I1/3 + k (sigma1 - sigma2),
 //   lambda_3 = I1/3 + k (2 sigma2 + sigma1),  k = 2 r / (3 sqrt 3).
 // ---------------------------------------------------------------------------
+// sin and cos on [0, pi/6] from their Taylor series about 0 (Horner in x^2):
+// the first omitted terms, x^11/11! and x^10/10!, are below 1e-10 there, far
+// under half a binary32 ulp of the results; only rounding (about 1 ulp) is
+// left.  Replaces the library sincosf, whose general argument reduction is
+// never needed for this range.
+__device__ __forceinline__ void sincos_small(float x, float &sn, float &cs) {
+  const float z = x * x;
+  float ps = fmaf(z, 2.7557319e-6f, -1.9841270e-4f);     // 1/9!, -1/7!
+  ps = fmaf(z, ps, 8.3333333e-3f);                       // 1/5!
+  ps = fmaf(z, ps, -1.6666667e-1f);                      // -1/3!
+  sn = fmaf(x * z, ps, x);
+  float pc = fmaf(z, 2.4801587e-5f, -1.3888889e-3f);     // 1/8!, -1/6!
+  pc = fmaf(z, pc, 4.1666667e-2f);                       // 1/4!
+  pc = fmaf(z, pc, -0.5f);                               // -1/2!
+  cs = fmaf(z, pc, 1.0f);
+}
+
 struct EigC {
   float l1, l2, l3, r, sigma1, sigma2, I1;
   bool j2_clamped, d_clamped;
@@ -330,7 +361,7 @@ __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
   const float y = sqrtf(27.0f * fmaxf(dd, 0.0f));
   const float pt = atan2f(y, fabsf(x)) * (1.0f / 3.0f);
   float st, ct;
-  sincosf(pt, &st, &ct);
+  sincos_small(pt, st, ct);
   st = fmaxf(st, 0.0f);
   const float other = fmaf(0.86602540378443864676f, ct, -0.5f * st);
   const bool pos = !(x < 0.0f);
@@ -348,11 +379,11 @@ __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
 // Unscaled binary64 invariants (I1, J2, J3, Delta) from the compensated pairs.
 __device__ __forceinline__ void invariants_out(const InvC &v, double *o) {
   const double s = ldexp(1.0, v.e);
-  o[0] = (double)v.I1.h + (double)v.I1.l;
-  o[1] = ((double)v.J2x6.h + (double)v.J2x6.l) / 6.0 * (s * s);
-  o[2] = ((double)v.J3x27.h + (double)v.J3x27.l) / 27.0 * (s * s * s);
+  o[0] = (double)v.I1.s + (double)v.I1.c;
+  o[1] = ((double)v.J2x6.s + (double)v.J2x6.c) / 6.0 * (s * s);
+  o[2] = ((double)v.J3x27.s + (double)v.J3x27.c) / 27.0 * (s * s * s);
   const double s3 = s * s * s;
-  o[3] = ((double)v.D.h + (double)v.D.l) * s3 * s3;
+  o[3] = ((double)v.D.s + (double)v.D.c) * s3 * s3;
 }
 
 // ---------------------------------------------------------------------------
@@ -394,9 +425,9 @@ __device__ __forceinline__ void grad_general_c(const float (&a)[9], const AdjC &
   const float ir = s.inv_r;
   const F2 d0 = two_sum(a[0], -a[4]), d1 = two_sum(a[0], -a[8]), d2 = two_sum(a[4], -a[8]);
   const float ir3 = ir * (1.0f / 3.0f);
-  const float S00 = round1(done(start(d0) + d1)) * ir3;
-  const float S11 = round1(done(start(d2) - d0)) * ir3;
-  const float S22 = -round1(done(start(d1) + d2)) * ir3;
+  const float S00 = round1(start(d0) + d1) * ir3;
+  const float S11 = round1(start(d2) - d0) * ir3;
+  const float S22 = -round1(start(d1) + d2) * ir3;
   const float S01 = a[1] * ir, S02 = a[2] * ir, S10 = a[3] * ir;
   const float S12 = a[5] * ir, S20 = a[6] * ir, S21 = a[7] * ir;
   const float C00 = det2(S11, S22, S12, S21);
@@ -425,9 +456,9 @@ __device__ __forceinline__ void grad_sym_c(const float (&s6)[6], const AdjC &s, 
   const float ir = s.inv_r;
   const F2 d0 = two_sum(s6[0], -s6[1]), d1 = two_sum(s6[0], -s6[2]), d2 = two_sum(s6[1], -s6[2]);
   const float ir3 = ir * (1.0f / 3.0f);
-  const float S00 = round1(done(start(d0) + d1)) * ir3;
-  const float S11 = round1(done(start(d2) - d0)) * ir3;
-  const float S22 = -round1(done(start(d1) + d2)) * ir3;
+  const float S00 = round1(start(d0) + d1) * ir3;
+  const float S11 = round1(start(d2) - d0) * ir3;
+  const float S22 = -round1(start(d1) + d2) * ir3;
   const float S12 = s6[3] * ir, S02 = s6[4] * ir, S01 = s6[5] * ir;
   const float C00 = det2(S11, S22, S12, S12);
   const float C11 = det2(S00, S22, S02, S02);

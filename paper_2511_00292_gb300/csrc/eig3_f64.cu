@@ -2,17 +2,19 @@
 // + statistics) and the adjoint, for the general 9-entry and symmetric
 // 6-entry layouts with binary64 or binary32 storage.
 //
-// One thread per matrix, grid-stride over the batch with a grid sized to fill
-// every SM once.  The binary64 path is bound by the FP64 pipe (two DFMA per
-// SM per clock on GB300, far below what HBM could feed), so the kernels keep
-// the memory side simple -- each thread reads its row with read-only loads
-// that the L1 merges -- and spend the design effort on the FP64 instruction
-// count (see eig3_f64.cuh).
+// One thread per matrix.  Blocks of 256 threads walk the batch in tiles of 256
+// rows (grid-stride over tiles, grid sized to fill every SM).  The input rows
+// of the next tile are copied into shared memory with asynchronous 16-byte
+// copies while the current tile is computed (eig3_tile.cuh); the adjoint
+// inputs (16- or 32-byte rows) move with direct vector accesses and the
+// outputs are stored directly.  The binary64 path is bound by the FP64 pipe
+// (two DFMA per SM per clock on GB300, far below what HBM could feed).
 #include <cstdint>
 
 #include "eig3_f64.cuh"
 #include "eig3_internal.h"
 #include "eig3_stats.cuh"
+#include "eig3_tile.cuh"
 
 namespace eig3 {
 namespace {
@@ -68,29 +70,103 @@ __global__ void __launch_bounds__(kThreads) k_invariants(const T *__restrict__ A
   }
 }
 
+// aux rows (r, sigma1, sigma2, I1): 32 B (binary64) or 16 B (binary32), so
+// 16-byte aligned whenever the base is; one or two vector accesses per row.
+template <typename T>
+__device__ __forceinline__ void store_aux(T *__restrict__ aux, int64_t i, bool vec,
+                                          const double (&x)[4]) {
+  if constexpr (sizeof(T) == 8) {
+    if (vec) {
+      double2 *q = reinterpret_cast<double2 *>(aux + 4 * i);
+      q[0] = make_double2(x[0], x[1]);
+      q[1] = make_double2(x[2], x[3]);
+      return;
+    }
+  } else {
+    if (vec) {
+      *reinterpret_cast<float4 *>(aux + 4 * i) =
+          make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+      return;
+    }
+  }
+  T *q = aux + 4 * i;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) q[j] = (T)x[j];
+}
+
+template <typename T>
+__device__ __forceinline__ void load_aux(const T *__restrict__ aux, int64_t i, bool vec,
+                                         double &r, double &s1, double &s2) {
+  if constexpr (sizeof(T) == 8) {
+    if (vec) {
+      const double2 *q = reinterpret_cast<const double2 *>(aux + 4 * i);
+      const double2 a = __ldg(q), b = __ldg(q + 1);
+      r = a.x;
+      s1 = a.y;
+      s2 = b.x;
+      return;
+    }
+  } else {
+    if (vec) {
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(aux + 4 * i));
+      r = a.x;
+      s1 = a.y;
+      s2 = a.z;
+      return;
+    }
+  }
+  r = (double)__ldg(aux + 4 * i);
+  s1 = (double)__ldg(aux + 4 * i + 1);
+  s2 = (double)__ldg(aux + 4 * i + 2);
+}
+
+__device__ __forceinline__ bool aligned16(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
 template <int LAYOUT, typename T, bool AUX, bool STATS>
 __global__ void __launch_bounds__(kThreads)
     k_eigvals(const T *__restrict__ A, int64_t n, T *__restrict__ lam, T *__restrict__ aux,
               eig3_stats *__restrict__ stats) {
   constexpr int N = Width<LAYOUT>::N;
+  __shared__ __align__(16) T sA[2][kTile * N];
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double a[N];
-    load_row<T, N>(A, i, a);
-    const Inv v = invariants_of<LAYOUT, N>(a);
-    const Eig e = eigvals_from_inv(v);
-    const double l[3] = {e.l1, e.l2, e.l3};
-    store_row<T, 3>(lam, i, l);
-    if constexpr (AUX) {
-      const double x[4] = {e.r, e.sigma1, e.sigma2, v.I1};
-      store_row<T, 4>(aux, i, x);
+  const bool vaux = AUX && aligned16(aux);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles)
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kTile;
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();  // tile t is in sA[buf]; every thread is done with sA[buf ^ 1]
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) {
+      double a[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = (double)sA[buf][threadIdx.x * N + j];
+      const Inv v = invariants_of<LAYOUT, N>(a);
+      const Eig e = eigvals_from_inv(v);
+      const int64_t i = r0 + threadIdx.x;
+      lam[3 * i + 0] = (T)e.l1;
+      lam[3 * i + 1] = (T)e.l2;
+      lam[3 * i + 2] = (T)e.l3;
+      if constexpr (AUX) {
+        const double x[4] = {e.r, e.sigma1, e.sigma2, v.I1};
+        store_aux<T>(aux, i, vaux, x);
+      }
+      if constexpr (STATS) {
+        stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
+                 (float)fmin(e.sigma1, e.sigma2), (T)e.l1, (T)e.l2, (T)e.l3);
+      }
     }
-    if constexpr (STATS) {
-      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
-               (float)fmin(e.sigma1, e.sigma2), (T)e.l1, (T)e.l2, (T)e.l3);
-    }
+    buf ^= 1;
   }
   if constexpr (STATS) stat_flush(acc, stats);
 }
@@ -100,33 +176,57 @@ __global__ void __launch_bounds__(kThreads)
     k_backward(const T *__restrict__ A, int64_t n, const T *__restrict__ g,
                const T *__restrict__ aux, T *__restrict__ gA) {
   constexpr int N = Width<LAYOUT>::N;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double a[N];
-    load_row<T, N>(A, i, a);
-    double gb[3];
-    load_row<T, 3>(g, i, gb);
-    double r, s1, s2;
-    if constexpr (AUX) {
-      double x[4];
-      load_row<T, 4>(aux, i, x);
-      r = x[0];
-      s1 = x[1];
-      s2 = x[2];
-    } else {
-      const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
-      r = e.r;
-      s1 = e.sigma1;
-      s2 = e.sigma2;
+  __shared__ __align__(16) T sA[2][kTile * N];
+  __shared__ __align__(16) T sG[2][kTile * 3];
+  const bool vaux = AUX && aligned16(aux);
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles) {
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+    tile_issue(g, (int64_t)blockIdx.x * kTile * 3, rows_of(blockIdx.x) * 3, sG[0]);
+  }
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kTile;
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) {
+      tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+      tile_issue(g, tn * kTile * 3, rows_of(tn) * 3, sG[buf ^ 1]);
     }
-    const Adj s = adjoint_scalars(r, s1, s2, gb[0], gb[1], gb[2]);
-    double G[N];
-    if constexpr (LAYOUT == EIG3_GENERAL9) {
-      grad_general(a, s, G);
-    } else {
-      grad_sym(a, s, G);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) {
+      double a[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = (double)sA[buf][threadIdx.x * N + j];
+      const double g1 = (double)sG[buf][threadIdx.x * 3 + 0];
+      const double g2 = (double)sG[buf][threadIdx.x * 3 + 1];
+      const double g3 = (double)sG[buf][threadIdx.x * 3 + 2];
+      const int64_t i = r0 + threadIdx.x;
+      double r, s1, s2;
+      if constexpr (AUX) {
+        load_aux<T>(aux, i, vaux, r, s1, s2);
+      } else {
+        const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
+        r = e.r;
+        s1 = e.sigma1;
+        s2 = e.sigma2;
+      }
+      const Adj s = adjoint_scalars(r, s1, s2, g1, g2, g3);
+      double G[N];
+      if constexpr (LAYOUT == EIG3_GENERAL9) {
+        grad_general(a, s, G);
+      } else {
+        grad_sym(a, s, G);
+      }
+      T *q = gA + N * i;
+#pragma unroll
+      for (int j = 0; j < N; ++j) q[j] = (T)G[j];
     }
-    store_row<T, N>(gA, i, G);
+    buf ^= 1;
   }
 }
 

@@ -1,0 +1,60 @@
+// eig3_tile.cuh -- block-wide, double-buffered staging of array-of-structs
+// rows through shared memory with asynchronous 16-byte copies (cp.async), so
+// that global loads are coalesced 16-byte accesses that overlap the
+// arithmetic of the previous tile.
+//
+// A tile is kTile consecutive rows of W elements; its byte offset in global
+// memory is a multiple of kTile * W * sizeof(E), itself a multiple of 16, so
+// for a 16-byte aligned base every full 16-byte chunk of a tile is aligned.
+// The chunks go through cp.async.cg (L2 only, no L1 allocation); the ragged
+// remainder and misaligned bases use ordinary element loads.  Completion is
+// awaited with cp.async.wait_group, a hardware wait on the thread's own
+// copies, followed by a block barrier.  Rows are read from shared memory with a
+// stride of W elements, free of bank conflicts per half-warp for W = 9 (any
+// type) and W = 3, 6 (binary64).
+//
+// Usage per block (one barrier per tile):
+//   tile_issue(first tile -> buffer 0); cp_async_commit();
+//   for each tile t of this block:
+//     cp_async_wait_all(); __syncthreads();     // tile t landed, tile t-1 done
+//     tile_issue(next tile -> other buffer); cp_async_commit();
+//     compute tile t from its buffer
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eig3 {
+
+constexpr int kTile = 256;  // rows per tile = threads per block
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Start copying count elements g[e0 .. e0+count) into s[0 .. count).
+template <typename E>
+__device__ __forceinline__ void tile_issue(const E *__restrict__ g, int64_t e0, int count,
+                                           E *__restrict__ s) {
+  const E *src = g + e0;
+  int head = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    const int n16 = (count * (int)sizeof(E)) >> 4;
+    const char *s8 = reinterpret_cast<const char *>(src);
+    char *d8 = reinterpret_cast<char *>(s);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) cp_async16(d8 + 16 * i, s8 + 16 * i);
+    head = (n16 << 4) / (int)sizeof(E);
+  }
+  for (int i = head + threadIdx.x; i < count; i += blockDim.x) s[i] = __ldg(src + i);
+}
+
+}  // namespace eig3

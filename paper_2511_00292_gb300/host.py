@@ -1,0 +1,78 @@
+"""Host-resident batches: stream chunks through the GPU.
+
+For a batch that lives in page-locked host memory, `HostPipeline` runs the
+library's forward and adjoint on fixed-size chunks with three CUDA streams:
+host-to-device copies of chunk i+1, the kernels on chunk i and the
+device-to-host copies of chunk i-1 overlap, so the step costs about the
+slowest of the three instead of their sum.  The device slots are allocated
+once per pipeline with torch (plumbing; the kernels only see their inputs and
+outputs).  Every computation is a call of the C ABI.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import eigvals, eigvals_backward, layout_of
+
+
+class HostPipeline:
+    def __init__(self, device=None, chunk: int = 1 << 24, depth: int = 2):
+        self.dev = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.chunk = int(chunk)
+        self.depth = int(depth)
+        self.s_in = torch.cuda.Stream(self.dev)
+        self.s_run = torch.cuda.Stream(self.dev)
+        self.s_out = torch.cuda.Stream(self.dev)
+        self._slots = {}
+
+    def _get_slots(self, key, width, dtype):
+        if key not in self._slots:
+            c, d = self.chunk, self.depth
+            mk = lambda w: [torch.empty((c, w), dtype=dtype, device=self.dev) for _ in range(d)]
+            self._slots[key] = dict(A=mk(width), w=mk(3), lam=mk(3), aux=mk(4), g=mk(width),
+                                    free=[torch.cuda.Event() for _ in range(d)],
+                                    loaded=[torch.cuda.Event() for _ in range(d)],
+                                    done=[torch.cuda.Event() for _ in range(d)])
+        return self._slots[key]
+
+    def forward_backward(self, A: torch.Tensor, w: torch.Tensor, lam_out: torch.Tensor,
+                         grad_out: torch.Tensor, layout=None, precision="f64"):
+        """Eigenvalues of every row of the pinned host tensor A into lam_out and the
+        gradient of sum(w * lambda) into grad_out (both pinned host tensors).
+        Asynchronous with respect to the host; ordered after the current stream's
+        pending work, and the current stream waits for the last copy."""
+        for t in (A, w, lam_out, grad_out):
+            if t.is_cuda or not t.is_pinned():
+                raise ValueError("HostPipeline works on pinned host tensors")
+        lay = layout_of(A, layout)
+        width = 9 if lay == 0 else 6
+        X = A.reshape(-1, width)
+        n = X.shape[0]
+        slots = self._get_slots((width, A.dtype), width, A.dtype)
+        main = torch.cuda.current_stream(self.dev)
+        for s in (self.s_in, self.s_run, self.s_out):
+            s.wait_stream(main)
+        for i, lo in enumerate(range(0, n, self.chunk)):
+            hi = min(n, lo + self.chunk)
+            m = hi - lo
+            k = i % self.depth
+            dA, dw = slots["A"][k][:m], slots["w"][k][:m]
+            dl, da, dg = slots["lam"][k][:m], slots["aux"][k][:m], slots["g"][k][:m]
+            with torch.cuda.stream(self.s_in):
+                if i >= self.depth:
+                    self.s_in.wait_event(slots["free"][k])
+                dA.copy_(X[lo:hi], non_blocking=True)
+                dw.copy_(w[lo:hi], non_blocking=True)
+                slots["loaded"][k].record(self.s_in)
+            with torch.cuda.stream(self.s_run):
+                self.s_run.wait_event(slots["loaded"][k])
+                eigvals(dA, layout=lay, precision=precision, return_aux=True, out=dl, aux_out=da)
+                eigvals_backward(dA, dw, aux=da, layout=lay, precision=precision, out=dg)
+                slots["done"][k].record(self.s_run)
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(slots["done"][k])
+                lam_out[lo:hi].copy_(dl, non_blocking=True)
+                grad_out.reshape(-1, width)[lo:hi].copy_(dg, non_blocking=True)
+                slots["free"][k].record(self.s_out)
+        main.wait_stream(self.s_out)

@@ -280,3 +280,29 @@ def test_zero_copy_pinned_host_buffers(eig3):
     assert torch.equal(l_h, eig3.eigvals(S.to(dev()), precision="f32c").cpu())
     with pytest.raises(ValueError):
         eig3.eigvals(bt.A)          # pageable host memory is refused
+
+
+def test_host_pipeline_matches_device(eig3):
+    """Chunked host-to-device streaming gives the device results bit for bit,
+    including a ragged last chunk and more chunks than device slots."""
+    from paper_2511_00292_gb300.host import HostPipeline
+    bt = W.workload4(n=10_007, device="cpu", seed=2200)
+    hA, hw = bt.A.pin_memory(), bt.extra["w"].pin_memory()
+    lam = torch.empty(bt.n, 3, dtype=torch.float64).pin_memory()
+    grad = torch.empty_like(hA).pin_memory()
+    pipe = HostPipeline(dev(), chunk=1024, depth=2)
+    pipe.forward_backward(hA, hw, lam, grad)
+    torch.cuda.synchronize()
+    dA = bt.A.to(dev())
+    l_d, a_d = eig3.eigvals(dA, return_aux=True)
+    g_d = eig3.eigvals_backward(dA, bt.extra["w"].to(dev()), aux=a_d)
+    assert torch.equal(lam, l_d.cpu()) and torch.equal(grad, g_d.cpu())
+    S = W.workload3(n=5_003, device="cpu", seed=2201).A
+    wS = torch.randn(S.shape[0], 3, dtype=torch.float32)
+    lS = torch.empty(S.shape[0], 3, dtype=torch.float32).pin_memory()
+    gS = torch.empty_like(S).pin_memory()
+    pipe.forward_backward(S.pin_memory(), wS.pin_memory(), lS, gS, precision="f32c")
+    torch.cuda.synchronize()
+    l2, a2 = eig3.eigvals(S.to(dev()), precision="f32c", return_aux=True)
+    g2 = eig3.eigvals_backward(S.to(dev()), wS.to(dev()), aux=a2, precision="f32c")
+    assert torch.equal(lS, l2.cpu()) and torch.equal(gS, g2.cpu())
