@@ -49,9 +49,9 @@ WORKLOAD = ("mixed fwd+bwd, 2^28 matrices/GPU: 2^27 symmetric 6-entry FP32 (comp
 # They describe the kernel source whose hash is recorded here; when the source
 # changes they are reported as stale and the traffic as null.
 FWD_F64_COUNTERS = {
-    "source_md5": "7d0a2c13b0cdbe16ae649d5f474e031e",
-    "fp64_pipe_inst": 196.11, "dfma": 89.0, "dmul": 73.0, "dadd": 19.0,
-    "dram_bytes": (302.071296e6 + 194.999296e6) / 4194304,
+    "source_md5": "7429854c0d4f0285fe35f5a0704efe5c",
+    "fp64_pipe_inst": 187.11, "dfma": 89.0, "dmul": 72.0, "dadd": 19.0,
+    "dram_bytes": (302.544128e6 + 193.488128e6) / 4194304,
 }
 FWD_F64_SOURCES = ("eig3_f64.cuh", "eig3_f64.cu", "eig3_stats.cuh")
 # FP64 pipe of GB300: 2 FMA lanes per SM (measured with a DFMA loop: 0.598 T
@@ -414,7 +414,16 @@ def measure_paths(eig3, W, dev, stream, steps):
 
     t4 = timed(fb, steps, stream)
     paths["fwd_bwd_f64_general9_2^24"] = {"G_matrices_per_s": b4.n / t4 / 1e6, "ms": t4}
-    del b4, lam4, aux4, g4
+    P4 = torch.empty(b4.n, 27, dtype=torch.float64, device=dev)
+    tp = timed(lambda: eig3.eigprojectors(b4.A, out=P4, return_eigvals=True, lam_out=lam4),
+               steps, stream)
+    paths["eigprojectors_f64_general9_2^24"] = {"G_matrices_per_s": b4.n / tp / 1e6, "ms": tp}
+    del b4, lam4, aux4, g4, P4
+    b3 = W.workload3(n=1 << 25, device=dev)
+    P3 = torch.empty(b3.n, 27, dtype=torch.float32, device=dev)
+    tq = timed(lambda: eig3.eigprojectors(b3.A, precision="f32c", out=P3), steps, stream)
+    paths["eigprojectors_f32c_sym6_2^25"] = {"G_matrices_per_s": b3.n / tq / 1e6, "ms": tq}
+    del b3, P3
     torch.cuda.empty_cache()
     return paths
 

@@ -140,6 +140,25 @@ eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int prec
                                   const void *grad_lam, const void *aux, void *grad_A,
                                   void *stream);
 
+/*
+ * eig3_eigprojectors -- eigenvalues and eigenprojectors E_1, E_2, E_3.
+ * Section 1 of the paper relates the eigenprojectors to the eigenvalue
+ * derivatives, E_k^T = d lambda_k / dA; with the Jacobians of J2 and J3
+ * (Lemmas of Sections J2 and J3) this gives
+ *   E_k = I/3 + a_J2(k) dev(A) + a_J3(k) dev(cof(dev A))^T,
+ * with (a_J2(k), a_J3(k)) the adjoint scalars of eig3_eigvals_backward for
+ * the weights e_k.  sum_k E_k = I, E_j E_k = delta_jk E_k and A E_k = lambda_k E_k
+ * for distinct eigenvalues.  Where two computed eigenvalues coincide exactly
+ * each of them gets half the projector onto their joint eigenspace (the
+ * cluster-mean convention of the adjoint).
+ *   A    device, n matrices (read only).
+ *   lam  device, n x 3 of `dtype` (ascending eigenvalues), or NULL.
+ *   P    device, n x 3 x 9 of `dtype`: P[27 i + 9 k + 3 r + c] = (E_{k+1})_{rc}
+ *        of matrix i (row-major 3 x 3, also for EIG3_SYM6 input).
+ */
+eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precision, int64_t n,
+                               void *lam, void *P, void *stream);
+
 /* Set a device eig3_stats to (0, 0, 0, +inf, 0) on `stream`. */
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream);
 

@@ -22,8 +22,8 @@ from . import _lib
 from ._lib import (F32, F64, GENERAL9, PREC_F32_COMP, PREC_F64, SYM6, Eig3Error, Eig3Stats,
                    check, load)
 
-__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "Stats", "Eig3Error",
-           "layout_of", "GENERAL9", "SYM6"]
+__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors", "Stats",
+           "Eig3Error", "layout_of", "GENERAL9", "SYM6"]
 
 _LAYOUTS = {"general9": GENERAL9, "sym6": SYM6, GENERAL9: GENERAL9, SYM6: SYM6}
 _PRECS = {"f64": PREC_F64, "f32c": PREC_F32_COMP, PREC_F64: PREC_F64,
@@ -163,6 +163,25 @@ def eigvals_backward(A: torch.Tensor, grad_lam: torch.Tensor, aux=None, layout=N
                                           _stream(dev))
     check(st, "eig3_eigvals_backward")
     return gA
+
+
+def eigprojectors(A: torch.Tensor, layout=None, precision="f64", return_eigvals=False,
+                  out=None, lam_out=None, device=None):
+    """Eigenprojectors E_1, E_2, E_3 (n, 3, 3, 3) with E_k^T = d lambda_k / dA
+    (ascending order); optionally also the eigenvalues (n, 3)."""
+    lay = layout_of(A, layout)
+    X = _rows(A, lay)
+    n = X.shape[0]
+    dev = _device(X, device)
+    P = out if out is not None else _alloc((n, 3, 3, 3), X.dtype, X, dev)
+    lam = None
+    if return_eigvals:
+        lam = lam_out if lam_out is not None else _alloc((n, 3), X.dtype, X, dev)
+    with torch.cuda.device(dev):
+        st = load().eig3_eigprojectors(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n,
+                                       _ptr(lam), _ptr(P), _stream(dev))
+    check(st, "eig3_eigprojectors")
+    return (P, lam) if return_eigvals else P
 
 
 class _Eig3Fn(torch.autograd.Function):

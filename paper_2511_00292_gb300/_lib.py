@@ -12,6 +12,7 @@ EXPORTS = (
     "eig3_invariants",
     "eig3_eigvals",
     "eig3_eigvals_backward",
+    "eig3_eigprojectors",
     "eig3_stats_reset",
     "eig3_status_string",
     "eig3_version",
@@ -68,6 +69,8 @@ def load():
         lib.eig3_eigvals.restype = I
         lib.eig3_eigvals_backward.argtypes = [P, I, I, I, I64, P, P, P, P]
         lib.eig3_eigvals_backward.restype = I
+        lib.eig3_eigprojectors.argtypes = [P, I, I, I, I64, P, P, P]
+        lib.eig3_eigprojectors.restype = I
         lib.eig3_stats_reset.argtypes = [P, P]
         lib.eig3_stats_reset.restype = I
         lib.eig3_status_string.argtypes = [I]

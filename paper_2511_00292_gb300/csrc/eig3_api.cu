@@ -144,6 +144,20 @@ eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int prec
   return from_cuda(eig3::launch_backward_f64(A, layout, dtype, n, grad_lam, aux, grad_A, s));
 }
 
+eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precision, int64_t n,
+                               void *lam, void *P, void *stream) {
+  eig3_status st = check_modes(layout, dtype, precision, n);
+  if (st != EIG3_OK) return st;
+  if (n == 0) return EIG3_OK;
+  if (!A || !P) return EIG3_ERR_ARG;
+  const size_t es = elem_size(dtype);
+  if (!aligned(A, es) || !aligned(P, es) || (lam && !aligned(lam, es))) return EIG3_ERR_ALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == EIG3_PREC_F32_COMP)
+    return from_cuda(eig3::launch_projectors_f32c(A, layout, n, lam, P, s));
+  return from_cuda(eig3::launch_projectors_f64(A, layout, dtype, n, lam, P, s));
+}
+
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream) {
   if (!stats) return EIG3_ERR_ARG;
   if (!aligned(stats, 8)) return EIG3_ERR_ALIGN;

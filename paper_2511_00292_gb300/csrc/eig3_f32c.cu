@@ -181,6 +181,61 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <int LAYOUT, bool LAM>
+__global__ void __launch_bounds__(kThreads)
+    k_projectors_c(const float *__restrict__ A, int64_t n, float *__restrict__ lam,
+                   float *__restrict__ P) {
+  constexpr int N = WidthC<LAYOUT>::N;
+  __shared__ __align__(16) float sA[2][kTile * N];
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles)
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kTile;
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) {
+      float a[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
+      const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+      const int64_t i = r0 + threadIdx.x;
+      if constexpr (LAM) {
+        lam[3 * i + 0] = e.l1;
+        lam[3 * i + 1] = e.l2;
+        lam[3 * i + 2] = e.l3;
+      }
+      float E[27];
+      projectors_c<N>(a, adjoint_units_c(e.r, e.sigma1, e.sigma2), E);
+      float *q = P + 27 * i;
+#pragma unroll
+      for (int j = 0; j < 27; ++j) q[j] = E[j];
+    }
+    buf ^= 1;
+  }
+}
+
+template <int LAYOUT>
+cudaError_t proj_c(const void *A, int64_t n, void *lam, void *P, cudaStream_t s) {
+  if (lam) {
+    auto k = k_projectors_c<LAYOUT, true>;
+    k<<<grid_for((const void *)k, kThreads, 0, n), kThreads, 0, s>>>((const float *)A, n,
+                                                                      (float *)lam, (float *)P);
+  } else {
+    auto k = k_projectors_c<LAYOUT, false>;
+    k<<<grid_for((const void *)k, kThreads, 0, n), kThreads, 0, s>>>((const float *)A, n,
+                                                                      (float *)lam, (float *)P);
+  }
+  return cudaGetLastError();
+}
+
 template <int LAYOUT>
 cudaError_t inv_c(const void *A, int64_t n, double *inv, cudaStream_t s) {
   auto k = k_invariants_c<LAYOUT>;
@@ -237,6 +292,12 @@ cudaError_t launch_eigvals_f32c(const void *A, int layout, int64_t n, void *lam,
                                 eig3_stats *stats, cudaStream_t s) {
   return layout == EIG3_GENERAL9 ? eig_c<EIG3_GENERAL9>(A, n, lam, aux, stats, s)
                                  : eig_c<EIG3_SYM6>(A, n, lam, aux, stats, s);
+}
+
+cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *lam, void *P,
+                                   cudaStream_t s) {
+  return layout == EIG3_GENERAL9 ? proj_c<EIG3_GENERAL9>(A, n, lam, P, s)
+                                 : proj_c<EIG3_SYM6>(A, n, lam, P, s);
 }
 
 cudaError_t launch_backward_f32c(const void *A, int layout, int64_t n, const void *grad_lam,

@@ -410,8 +410,10 @@ __device__ __forceinline__ AdjC adjoint_c(float r, float sigma1, float sigma2, f
   const float g12 = k2 * sigma1;
   const float g23 = k2 * sigma2;
   const float g13 = k2 * (sigma1 + sigma2);
-  const float D12 = (g12 != 0.0f) ? (g2 - g1) / g12 : 0.0f;
-  const float D23 = (g23 != 0.0f) ? (g3 - g2) / g23 : 0.0f;
+  const bool z1 = g12 == 0.0f, z2 = g23 == 0.0f;
+  // an exactly coalesced pair takes the mean of its two weights
+  const float D12 = z1 ? 0.0f : ((z2 ? 0.5f * (g2 + g3) : g2) - g1) / g12;
+  const float D23 = z2 ? 0.0f : (g3 - (z1 ? 0.5f * (g1 + g2) : g2)) / g23;
   AdjC o;
   o.aJ3r2 = (g13 != 0.0f) ? (D23 - D12) / g13 : 0.0f;
   o.aJ2r = fmaf(-0.38490017945975050967f * fmaf(2.0f, sigma1, sigma2), o.aJ3r2, D23);
@@ -419,6 +421,76 @@ __device__ __forceinline__ AdjC adjoint_c(float r, float sigma1, float sigma2, f
   // r below the normal range counts as a triple eigenvalue
   o.inv_r = (r >= 1.17549435e-38f) ? 1.0f / r : 0.0f;
   return o;
+}
+
+// Adjoint scalars for the unit weights e_1, e_2, e_3 (eigenprojectors), as in
+// the binary64 path.
+struct Adj3C {
+  float b2[3], b3[3], inv_r;
+};
+
+__device__ __forceinline__ Adj3C adjoint_units_c(float r, float sigma1, float sigma2) {
+  const float h = 0.86602540378443864676f;  // sqrt3 / 2
+  const bool z1 = sigma1 == 0.0f, z2 = sigma2 == 0.0f;
+  const float X12 = z1 ? 0.0f : h / sigma1;
+  const float X23 = z2 ? 0.0f : h / sigma2;
+  const float X13 = h / (sigma1 + sigma2);
+  const float c = -0.38490017945975050967f * fmaf(2.0f, sigma1, sigma2);
+  Adj3C o;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float g1 = k == 0 ? 1.0f : 0.0f, g2 = k == 1 ? 1.0f : 0.0f, g3 = k == 2 ? 1.0f : 0.0f;
+    const float D12 = z1 ? 0.0f : ((z2 ? 0.5f * (g2 + g3) : g2) - g1) * X12;
+    const float D23 = z2 ? 0.0f : (g3 - (z1 ? 0.5f * (g1 + g2) : g2)) * X23;
+    o.b3[k] = (D23 - D12) * X13;
+    o.b2[k] = fmaf(c, o.b3[k], D23);
+  }
+  o.inv_r = (r >= 1.17549435e-38f) ? 1.0f / r : 0.0f;
+  return o;
+}
+
+// E_k = I/3 + (r a_J2) S^ + (r^2 a_J3) dev(cof S^)^T, S^ = dev(A)/r, 27 values.
+template <int N>
+__device__ __forceinline__ void projectors_c(const float (&a)[N], const Adj3C &s, float (&E)[27]) {
+  const float ir = s.inv_r;
+  F2 d0, d1, d2;
+  float S01, S02, S10, S12, S20, S21;
+  if constexpr (N == 9) {
+    d0 = two_sum(a[0], -a[4]);
+    d1 = two_sum(a[0], -a[8]);
+    d2 = two_sum(a[4], -a[8]);
+    S01 = a[1] * ir;
+    S02 = a[2] * ir;
+    S10 = a[3] * ir;
+    S12 = a[5] * ir;
+    S20 = a[6] * ir;
+    S21 = a[7] * ir;
+  } else {
+    d0 = two_sum(a[0], -a[1]);
+    d1 = two_sum(a[0], -a[2]);
+    d2 = two_sum(a[1], -a[2]);
+    S12 = S21 = a[3] * ir;
+    S02 = S20 = a[4] * ir;
+    S01 = S10 = a[5] * ir;
+  }
+  const float ir3 = ir * (1.0f / 3.0f);
+  const float S00 = round1(start(d0) + d1) * ir3;
+  const float S11 = round1(start(d2) - d0) * ir3;
+  const float S22 = -round1(start(d1) + d2) * ir3;
+  const float S[9] = {S00, S01, S02, S10, S11, S12, S20, S21, S22};
+  const float Ct[9] = {det2(S11, S22, S12, S21), det2(S02, S21, S01, S22), det2(S01, S12, S02, S11),
+                       det2(S12, S20, S10, S22), det2(S00, S22, S02, S20), det2(S02, S10, S00, S12),
+                       det2(S10, S21, S11, S20), det2(S01, S20, S00, S21), det2(S00, S11, S01, S10)};
+  const float tc = ((Ct[0] + Ct[4]) + Ct[8]) * (1.0f / 3.0f);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const bool diag = (j == 0 || j == 4 || j == 8);
+      const float cj = diag ? Ct[j] - tc : Ct[j];
+      E[9 * k + j] = fmaf(s.b2[k], S[j], fmaf(s.b3[k], cj, diag ? (1.0f / 3.0f) : 0.0f));
+    }
+  }
 }
 
 __device__ __forceinline__ void grad_general_c(const float (&a)[9], const AdjC &s, float (&G)[9]) {

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads)
       }
       if constexpr (STATS) {
         stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
-                 (float)fmin(e.sigma1, e.sigma2), (T)e.l1, (T)e.l2, (T)e.l3);
+                 seed_float(min_nonneg(e.sigma1, e.sigma2)), (T)e.l1, (T)e.l2, (T)e.l3);
       }
     }
     buf ^= 1;
@@ -230,6 +230,60 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <int LAYOUT, typename T, bool LAM>
+__global__ void __launch_bounds__(kThreads)
+    k_projectors(const T *__restrict__ A, int64_t n, T *__restrict__ lam, T *__restrict__ P) {
+  constexpr int N = Width<LAYOUT>::N;
+  __shared__ __align__(16) T sA[2][kTile * N];
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles)
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kTile;
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) {
+      double a[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = (double)sA[buf][threadIdx.x * N + j];
+      const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
+      const int64_t i = r0 + threadIdx.x;
+      if constexpr (LAM) {
+        lam[3 * i + 0] = (T)e.l1;
+        lam[3 * i + 1] = (T)e.l2;
+        lam[3 * i + 2] = (T)e.l3;
+      }
+      double E[27];
+      projectors<N>(a, adjoint_units(e.r, e.sigma1, e.sigma2), E);
+      T *q = P + 27 * i;
+#pragma unroll
+      for (int j = 0; j < 27; ++j) q[j] = (T)E[j];
+    }
+    buf ^= 1;
+  }
+}
+
+template <int LAYOUT, typename T>
+cudaError_t proj_launch(const void *A, int64_t n, void *lam, void *P, cudaStream_t s) {
+  if (lam) {
+    auto k = k_projectors<LAYOUT, T, true>;
+    k<<<grid_for((const void *)k, kThreads, 0, n), kThreads, 0, s>>>((const T *)A, n, (T *)lam,
+                                                                      (T *)P);
+  } else {
+    auto k = k_projectors<LAYOUT, T, false>;
+    k<<<grid_for((const void *)k, kThreads, 0, n), kThreads, 0, s>>>((const T *)A, n, (T *)lam,
+                                                                      (T *)P);
+  }
+  return cudaGetLastError();
+}
+
 template <int LAYOUT, typename T>
 cudaError_t inv_launch(const void *A, int64_t n, double *inv, cudaStream_t s) {
   auto k = k_invariants<LAYOUT, T>;
@@ -292,6 +346,15 @@ cudaError_t launch_eigvals_f64(const void *A, int layout, int dtype, int64_t n, 
                              : eig_launch<EIG3_GENERAL9, float>(A, n, lam, aux, stats, s);
   return dtype == EIG3_F64 ? eig_launch<EIG3_SYM6, double>(A, n, lam, aux, stats, s)
                            : eig_launch<EIG3_SYM6, float>(A, n, lam, aux, stats, s);
+}
+
+cudaError_t launch_projectors_f64(const void *A, int layout, int dtype, int64_t n, void *lam,
+                                  void *P, cudaStream_t s) {
+  if (layout == EIG3_GENERAL9)
+    return dtype == EIG3_F64 ? proj_launch<EIG3_GENERAL9, double>(A, n, lam, P, s)
+                             : proj_launch<EIG3_GENERAL9, float>(A, n, lam, P, s);
+  return dtype == EIG3_F64 ? proj_launch<EIG3_SYM6, double>(A, n, lam, P, s)
+                           : proj_launch<EIG3_SYM6, float>(A, n, lam, P, s);
 }
 
 cudaError_t launch_backward_f64(const void *A, int layout, int dtype, int64_t n,

@@ -51,6 +51,29 @@ __device__ __forceinline__ double pow2d(int k) {  // 2^k for -1022 <= k <= 1023
 // with the sign bit set give +0, like fmax(x, 0).
 __device__ __forceinline__ double nonneg(double x) { return __double2hiint(x) < 0 ? 0.0 : x; }
 
+// Conversions for the binary32 seed, done with integer operations: on GB300
+// the float<->double conversion instructions occupy the FP64 pipe, the
+// integer pipe is idle.
+// Non-negative double -> float, mantissa truncated (relative error < 2^-23);
+// values below the binary32 normal range give 0.
+__device__ __forceinline__ float seed_float(double x) {
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  const int f = ((e - 896) << 23) | ((hi & 0xfffff) << 3) | (int)((unsigned)__double2loint(x) >> 29);
+  return (e < 897) ? 0.0f : __int_as_float(f);
+}
+
+// Non-negative normal float -> double, exactly (0 for zero and subnormals).
+__device__ __forceinline__ double widen(float f) {
+  const int b = __float_as_int(f);
+  return ((b & 0x7f800000) == 0) ? 0.0 : __hiloint2double((b >> 3) + (896 << 20), b << 29);
+}
+
+// min of two non-negative doubles: their bit patterns order like their values.
+__device__ __forceinline__ double min_nonneg(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
+}
+
 // x < 0 (excluding -0) by the bits.
 __device__ __forceinline__ bool negative(double x) {
   const int hi = __double2hiint(x);
@@ -225,7 +248,8 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
 
 // --------------------------------------------------------------------------
 // Algorithm 6, angle part.  With x = 27 J3 and y = sqrt(27 Delta+) the triple
-// angle is phi = atan2(y, x) in [0, pi] (reading R2).  The kernel needs
+// angle is phi = atan2(y, x) in [0, pi] (reading R2); any positive multiple
+// of (x, y) gives the same angle, and the caller passes (J3, sqrt(Delta+/27)).  The kernel needs
 //   sigma1 = sin(phi / 3)          and   sigma2 = sin((pi - phi) / 3),
 // from which cos(phi/3) = (2 sigma2 + sigma1) / sqrt 3 and the three
 // eigenvalues follow without cancellation, and which are also the adjoint's
@@ -252,11 +276,11 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   const int e = min((h >> 20) & 0x7ff, 2045);
   const double sc = __hiloint2double((2046 - e) << 20, 0);
   const double X = ax * sc, Y = y * sc;
-  // binary32 seed w0 = c0 + i s0
-  const float pf = atan2f(__double2float_rn(Y), __double2float_rn(X)) * (1.0f / 3.0f);
+  // binary32 seed w0 = c0 + i s0 (pf in [0, pi/6], so c0, s0 >= 0)
+  const float pf = atan2f(seed_float(Y), seed_float(X)) * (1.0f / 3.0f);
   float sf, cf;
   __sincosf(pf, &sf, &cf);
-  const double c0 = (double)cf, s0 = (double)sf;
+  const double c0 = widen(cf), s0 = widen(fmaxf(sf, 0.0f));
   const double cc = c0 * c0, ss = s0 * s0;  // exact: 24-bit factors
   // w0^3 = c0 (c0^2 - 3 s0^2) + i s0 (3 c0^2 - s0^2)
   const double a3 = c0 * fma(-3.0, ss, cc);
@@ -264,7 +288,7 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   // rho = z conj(w0^3); its argument is 3 eps (|3 eps| ~ 1e-6: arg = Im/Re to 1e-18)
   const double re = fma(X, a3, Y * b3);
   const double im = fma(Y, a3, -(X * b3));
-  const double rc0 = (double)__frcp_rn(__double2float_rn(re));
+  const double rc0 = widen(__frcp_rn(seed_float(re)));
   const double rc = fma(rc0, fma(-re, rc0, 1.0), rc0);
   // z = 0 (re = +0): the angle is undetermined, keep phi = 0
   const double eps = (__double2hiint(re) > 0) ? (im * rc) * kInv3 : 0.0;
@@ -304,7 +328,8 @@ __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
   const double Dp = nonneg(v.D);
   o.r = sqrt(3.0 * J2p);
   if (v.e != 0) o.r *= pow2d(v.e);
-  triple_angle_sines(27.0 * v.J3, sqrt(27.0 * Dp), o.sigma1, o.sigma2);
+  // (J3, sqrt(Delta/27)) has the direction of (27 J3, sqrt(27 Delta))
+  triple_angle_sines(v.J3, sqrt(Dp * kInv27), o.sigma1, o.sigma2);
   const double k = o.r * kK;
   const double i3 = v.I1 * kInv3;
   o.l1 = fma(-k, fma(2.0, o.sigma1, o.sigma2), i3);
@@ -361,14 +386,109 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const double P = s12 * s3;
   const double R = 1.0 / (m * P);
   const double Rh = kHalfSqrt3 * (m * R);  // (sqrt3/2) / P
-  const double D12 = z1 ? 0.0 : (g2 - g1) * ((s2 * s3) * Rh);
-  const double D23 = z2 ? 0.0 : (g3 - g2) * ((s1 * s3) * Rh);
+  // an exactly coalesced pair takes the mean of its two weights
+  const double m12 = 0.5 * (g1 + g2), m23 = 0.5 * (g2 + g3);
+  const double D12 = z1 ? 0.0 : ((z2 ? m23 : g2) - g1) * ((s2 * s3) * Rh);
+  const double D23 = z2 ? 0.0 : (g3 - (z1 ? m12 : g2)) * ((s1 * s3) * Rh);
   Adj o;
   o.aJ3r2 = (D23 - D12) * (s12 * Rh);
   o.aJ2r = fma(-kK * fma(2.0, sigma1, sigma2), o.aJ3r2, D23);
   o.aI1 = ((g1 + g2) + g3) * kInv3;
   o.inv_r = rz ? 0.0 : (P * R) * p2k;
   return o;
+}
+
+// The adjoint scalars for the three unit weights e_1, e_2, e_3 at once (the
+// eigenprojectors), from the same single division: with X12 = (sqrt3/2)/s1,
+// X23 = (sqrt3/2)/s2, X13 = (sqrt3/2)/s3 and c = -kK (2 sigma1 + sigma2), for
+// distinct eigenvalues
+//   e_1: r^2 a_J3 =  X12 X13,          r a_J2 = c (r^2 a_J3)
+//   e_2: r^2 a_J3 = -(X12 + X23) X13,  r a_J2 = c (r^2 a_J3) - X23
+//   e_3: r^2 a_J3 =  X23 X13,          r a_J2 = c (r^2 a_J3) + X23
+// (each sums to 0 over k, so sum_k E_k = I exactly in real arithmetic); an
+// exactly coalesced pair shares the mean of its two weights.
+struct Adj3 {
+  double b2[3], b3[3], inv_r;
+};
+
+__device__ __forceinline__ Adj3 adjoint_units(double r, double sigma1, double sigma2) {
+  const bool z1 = hi_abs(sigma1) < (63 << 20);
+  const bool z2 = hi_abs(sigma2) < (63 << 20);
+  const double s1 = z1 ? 1.0 : sigma1, s2 = z2 ? 1.0 : sigma2;
+  const double s3 = sigma1 + sigma2;
+  const int hr = hi_abs(r);
+  const bool rz = hr < (1 << 20);
+  const int kr = min((hr >> 20) - 1023, 1022);
+  const double p2k = pow2d(-kr);
+  const double m = rz ? 1.0 : r * p2k;
+  const double s12 = s1 * s2;
+  const double P = s12 * s3;
+  const double R = 1.0 / (m * P);
+  const double Rh = kHalfSqrt3 * (m * R);
+  const double X12 = (s2 * s3) * Rh;
+  const double X23 = (s1 * s3) * Rh;
+  const double X13 = s12 * Rh;
+  const double c = -kK * fma(2.0, sigma1, sigma2);
+  Adj3 o;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // weights e_k, with an exactly coalesced pair taking the mean of its two
+    const double g1 = k == 0 ? 1.0 : 0.0, g2 = k == 1 ? 1.0 : 0.0, g3 = k == 2 ? 1.0 : 0.0;
+    const double D12 = z1 ? 0.0 : ((z2 ? 0.5 * (g2 + g3) : g2) - g1) * X12;
+    const double D23 = z2 ? 0.0 : (g3 - (z1 ? 0.5 * (g1 + g2) : g2)) * X23;
+    o.b3[k] = (D23 - D12) * X13;
+    o.b2[k] = fma(c, o.b3[k], D23);
+  }
+  o.inv_r = rz ? 0.0 : (P * R) * p2k;
+  return o;
+}
+
+// Eigenprojectors E_k = d lambda_k/dA ^T = I/3 + (r a_J2) S^ + (r^2 a_J3) dev(cof S^)^T
+// with S^ = dev(A)/r, written as 27 values (k-major, row-major 3 x 3).
+// Input: the 9 entries of a general matrix, or the 6 of a symmetric one.
+template <int N>
+__device__ __forceinline__ void projectors(const double (&a)[N], const Adj3 &s, double (&E)[27]) {
+  const double ir = s.inv_r;
+  double d0, d1, d2, S01, S02, S10, S12, S20, S21;
+  if constexpr (N == 9) {
+    d0 = a[0] - a[4];
+    d1 = a[0] - a[8];
+    d2 = a[4] - a[8];
+    S01 = a[1] * ir;
+    S02 = a[2] * ir;
+    S10 = a[3] * ir;
+    S12 = a[5] * ir;
+    S20 = a[6] * ir;
+    S21 = a[7] * ir;
+  } else {
+    d0 = a[0] - a[1];
+    d1 = a[0] - a[2];
+    d2 = a[1] - a[2];
+    S12 = S21 = a[3] * ir;
+    S02 = S20 = a[4] * ir;
+    S01 = S10 = a[5] * ir;
+  }
+  const double ir3 = ir * kInv3;
+  const double S00 = (d0 + d1) * ir3;
+  const double S11 = (d2 - d0) * ir3;
+  const double S22 = -(d1 + d2) * ir3;
+  const double S[9] = {S00, S01, S02, S10, S11, S12, S20, S21, S22};
+  // Ct = cof(S^)^T = adj(S^), row-major
+  const double Ct[9] = {fma(S11, S22, -(S12 * S21)), fma(S02, S21, -(S01 * S22)),
+                        fma(S01, S12, -(S02 * S11)), fma(S12, S20, -(S10 * S22)),
+                        fma(S00, S22, -(S02 * S20)), fma(S02, S10, -(S00 * S12)),
+                        fma(S10, S21, -(S11 * S20)), fma(S01, S20, -(S00 * S21)),
+                        fma(S00, S11, -(S01 * S10))};
+  const double tc = ((Ct[0] + Ct[4]) + Ct[8]) * kInv3;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const bool diag = (j == 0 || j == 4 || j == 8);
+      const double cj = diag ? Ct[j] - tc : Ct[j];
+      E[9 * k + j] = fma(s.b2[k], S[j], fma(s.b3[k], cj, diag ? kInv3 : 0.0));
+    }
+  }
 }
 
 // Gradient of a general matrix from the adjoint scalars, G[0..8] row-major.

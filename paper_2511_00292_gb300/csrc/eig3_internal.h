@@ -22,6 +22,8 @@ cudaError_t launch_invariants_f64(const void *A, int layout, int dtype, int64_t 
                                   cudaStream_t s);
 cudaError_t launch_eigvals_f64(const void *A, int layout, int dtype, int64_t n, void *lam,
                                void *aux, eig3_stats *stats, cudaStream_t s);
+cudaError_t launch_projectors_f64(const void *A, int layout, int dtype, int64_t n, void *lam,
+                                  void *P, cudaStream_t s);
 cudaError_t launch_backward_f64(const void *A, int layout, int dtype, int64_t n,
                                 const void *grad_lam, const void *aux, void *grad_A,
                                 cudaStream_t s);
@@ -31,6 +33,8 @@ cudaError_t launch_invariants_f32c(const void *A, int layout, int64_t n, double 
                                    cudaStream_t s);
 cudaError_t launch_eigvals_f32c(const void *A, int layout, int64_t n, void *lam, void *aux,
                                 eig3_stats *stats, cudaStream_t s);
+cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *lam, void *P,
+                                   cudaStream_t s);
 cudaError_t launch_backward_f32c(const void *A, int layout, int64_t n, const void *grad_lam,
                                  const void *aux, void *grad_A, cudaStream_t s);
 

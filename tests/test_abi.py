@@ -28,8 +28,8 @@ def declared_functions():
 
 def test_header_declares_the_api():
     names = declared_functions()
-    for n in ("eig3_invariants", "eig3_eigvals", "eig3_eigvals_backward", "eig3_stats_reset",
-              "eig3_status_string", "eig3_version"):
+    for n in ("eig3_invariants", "eig3_eigvals", "eig3_eigvals_backward", "eig3_eigprojectors",
+              "eig3_stats_reset", "eig3_status_string", "eig3_version"):
         assert n in names
 
 
@@ -92,6 +92,11 @@ def test_host_validation_without_gpu(lib):
     assert lib.eig3_eigvals(P(0x10002), 0, 1, 0, 5, ok_ptr, None, None, None) == 4
     assert lib.eig3_eigvals_backward(ok_ptr, 1, 1, 1, 5, P(0x10002), None, ok_ptr, None) == 4
     assert lib.eig3_invariants(ok_ptr, 0, 1, 0, 5, P(0x10004), None) == 4
+    # eigenprojectors
+    assert lib.eig3_eigprojectors(None, 0, 0, 0, 0, None, None, None) == 0
+    assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, None, None) == 1
+    assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, bad_ptr, None) == 4
+    assert lib.eig3_eigprojectors(ok_ptr, 2, 0, 0, 5, None, ok_ptr, None) == 2
     # stats reset
     assert lib.eig3_stats_reset(None, None) == 1
     assert lib.eig3_stats_reset(P(0x10004), None) == 4
