@@ -15,6 +15,7 @@ Function map (paper sections):
     eigvals_naive     Algorithm 6 on the naive invariants
     eigvals_grad      d lambda_k / dA = l r^T / (l^T r)  (Section 1, E_k^T)
     eigval_jacobians  the three d lambda_k / dA separately
+    mohr_coulomb      the yield function of the application section (+ gradient)
     bounds            first-order stability bounds, C = 1, Frobenius norm
     eigvals_mt        eigvals on POSIX threads, for timing on host cores
 """
@@ -68,6 +69,8 @@ def _load():
                 getattr(lib, name).restype = None
             lib.eig3o_eigvals_grad_batch.argtypes = [P, P, I64, I, P]
             lib.eig3o_eigvals_grad_batch.restype = None
+            lib.eig3o_mohr_coulomb_batch.argtypes = [P, I64, I, D, D, P, P]
+            lib.eig3o_mohr_coulomb_batch.restype = None
             lib.eig3o_eigval_jacobians_batch.argtypes = [P, I64, I, P]
             lib.eig3o_eigval_jacobians_batch.restype = None
             lib.eig3o_bounds_batch.argtypes = [P, P, I64, I, D, P]
@@ -141,6 +144,19 @@ def eigval_jacobians(X, layout: int = GENERAL9) -> np.ndarray:
     out = np.empty((X.shape[0], 27), dtype=np.float64)
     _load().eig3o_eigval_jacobians_batch(_ptr(X), X.shape[0], layout, _ptr(out))
     return out.reshape(-1, 3, 9)
+
+
+def mohr_coulomb(X, s_yc: float = 100.0, m: float = 10.0, layout: int = GENERAL9,
+                 grad: bool = False):
+    """Mohr-Coulomb yield value per matrix (Section "Application"), literal
+    max over the three principal-stress pairs; with grad=True also its
+    gradient with respect to the stored entries."""
+    X = _as_input(X, layout)
+    f = np.empty(X.shape[0], dtype=np.float64)
+    g = np.empty_like(X) if grad else None
+    _load().eig3o_mohr_coulomb_batch(_ptr(X), X.shape[0], layout, float(s_yc), float(m), _ptr(f),
+                                     _ptr(g) if grad else None)
+    return (f, g) if grad else f
 
 
 def bounds(X, kappa=None, layout: int = GENERAL9, u: float = U64) -> np.ndarray:

@@ -321,6 +321,35 @@ void eig3o_bounds(const double *A, double kappa, double u, double *out) {
 }
 
 /* ---------------------------------------------------------------------- */
+/* Mohr-Coulomb yield function (Section "Application"):                    */
+/*   f = (1/S_yc) ((m+1)/2) max_{i<j} (|s_i - s_j| + K (s_i + s_j)) - 1,    */
+/*   K = (m-1)/(m+1), s_k the principal stresses (the eigenvalues).         */
+/* The gradient is d f/d s_k of the maximising pair chained with           */
+/* d lambda_k / dA (eigenvector form).  out_grad may be NULL.              */
+/* ---------------------------------------------------------------------- */
+double eig3o_mohr_coulomb(const double *A, double s_yc, double m, double *out_grad) {
+  double s[3];
+  eig3o_eigvals(A, s);
+  double K = (m - 1.0) / (m + 1.0);
+  double best = -INFINITY;
+  int bi = 0, bj = 1;
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j) {
+      double v = fabs(s[i] - s[j]) + K * (s[i] + s[j]);
+      if (v > best) { best = v; bi = i; bj = j; }
+    }
+  double c = (m + 1.0) / 2.0 / s_yc;
+  if (out_grad) {
+    double g[3] = {0.0, 0.0, 0.0};
+    double sg = (s[bi] - s[bj] >= 0.0) ? 1.0 : -1.0;   /* d|s_i - s_j| */
+    g[bi] = c * (sg + K);
+    g[bj] = c * (-sg + K);
+    eig3o_eigvals_grad(A, g, out_grad);
+  }
+  return c * best - 1.0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Batched entry points (layout 0 = 9 entries, 1 = symmetric 6 entries).   */
 /* ---------------------------------------------------------------------- */
 static void load(const double *X, int64_t i, int layout, double *A) {
@@ -394,6 +423,29 @@ void eig3o_eigval_jacobians_batch(const double *X, int64_t n, int layout, double
   for (int64_t i = 0; i < n; ++i) {
     load(X, i, layout, A);
     eig3o_eigval_jacobians(A, out + 27 * i);
+  }
+}
+
+/* Mohr-Coulomb value per matrix, and its gradient with respect to the stored
+ * entries (layout as eig3o_eigvals_grad_batch) when gX is not NULL. */
+void eig3o_mohr_coulomb_batch(const double *X, int64_t n, int layout, double s_yc, double m,
+                              double *f, double *gX) {
+  double A[9], G[9];
+  for (int64_t i = 0; i < n; ++i) {
+    load(X, i, layout, A);
+    f[i] = eig3o_mohr_coulomb(A, s_yc, m, gX ? G : 0);
+    if (!gX) continue;
+    if (layout == 0) {
+      for (int j = 0; j < 9; ++j) gX[9 * i + j] = G[j];
+    } else {
+      double *g = gX + 6 * i;
+      g[0] = G[0];
+      g[1] = G[4];
+      g[2] = G[8];
+      g[3] = G[5] + G[7];
+      g[4] = G[2] + G[6];
+      g[5] = G[1] + G[3];
+    }
   }
 }
 

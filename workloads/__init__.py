@@ -301,6 +301,39 @@ def gradient_batch(n: int, device="cpu", seed: int = 2001, min_gap: float = 1e-2
     return Batch(A, "general9", kappa, lam)
 
 
+def lode_sweep(n: int, j2: float = 150.0) -> np.ndarray:
+    """The stress states of the paper's yield-function study (Section
+    "Application"): sigma = U_symm diag(s1, s2, s3) U_symm^T with
+    s_k = (2/3) sqrt(3 J2) cos(theta + 2 pi k / 3), theta evenly over [0, 2 pi),
+    J2 = 150 (MPa^2).  Returns (n, 6) symmetric rows (A00, A11, A22, A12, A02, A01)."""
+    U = paper_U("symm")
+    th = np.arange(n) * (2.0 * np.pi / n)
+    out = np.empty((n, 6))
+    for i, t in enumerate(th):
+        s = [(2.0 / 3.0) * np.sqrt(3.0 * j2) * np.cos(t + 2.0 * np.pi * k / 3.0) for k in (1, 2, 3)]
+        A = U @ np.diag(s) @ U.T
+        A = 0.5 * (A + A.T)
+        out[i] = [A[0, 0], A[1, 1], A[2, 2], A[1, 2], A[0, 2], A[0, 1]]
+    return out
+
+
+def stress_field(n: int, device="cpu", seed: int = 1006, scale: float = 100.0) -> Batch:
+    """Symmetric stress states of engineering magnitude (MPa): Haar rotations
+    of principal stresses with hydrostatic part p ~ U[-2, 1] scale, deviatoric
+    radius log-uniform in [1e-3, 1] scale and Lode angle U[0, 2 pi)."""
+    g = _gen(seed, device)
+    Q = haar_o3(n, g, device)
+    p = uniform(n, -2.0, 1.0, g, device) * scale
+    rad = log_uniform(n, 1e-3, 1.0, g, device) * scale
+    th = uniform(n, 0.0, 2.0 * math.pi, g, device)
+    k = torch.arange(1, 4, device=device, dtype=torch.float64)
+    lam = p.unsqueeze(1) + (2.0 / 3.0) * rad.unsqueeze(1) * torch.cos(
+        th.unsqueeze(1) + 2.0 * math.pi * k / 3.0)
+    A = symmetric_from_spectrum(lam, Q)
+    return Batch(to_sym6(A).contiguous(), "sym6", torch.ones(n, dtype=torch.float64,
+                                                             device=device), lam)
+
+
 def sample_indices(n: int, k: int, seed: int = 7) -> np.ndarray:
     """k sorted distinct indices in [0, n), always including the first and last."""
     rng = np.random.default_rng(seed)
