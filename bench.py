@@ -424,6 +424,20 @@ def measure_paths(eig3, W, dev, stream, steps):
     tq = timed(lambda: eig3.eigprojectors(b3.A, precision="f32c", out=P3), steps, stream)
     paths["eigprojectors_f32c_sym6_2^25"] = {"G_matrices_per_s": b3.n / tq / 1e6, "ms": tq}
     del b3, P3
+    # Mohr-Coulomb yield value + gradient (Section "Application"), fused
+    sf = W.stress_field(1 << 25, dev, seed=1006)
+    f5 = torch.empty(sf.n, dtype=torch.float64, device=dev)
+    g5 = torch.empty_like(sf.A)
+    tm = timed(lambda: eig3.mohr_coulomb(sf.A, grad=True, out=f5, grad_out=g5), steps, stream)
+    paths["mohr_coulomb_f64_sym6_2^25"] = {"G_matrices_per_s": sf.n / tm / 1e6, "ms": tm}
+    A32 = sf.A.float()
+    del sf, f5, g5
+    f6 = torch.empty(A32.shape[0], dtype=torch.float32, device=dev)
+    g6 = torch.empty_like(A32)
+    tn = timed(lambda: eig3.mohr_coulomb(A32, precision="f32c", grad=True, out=f6, grad_out=g6),
+               steps, stream)
+    paths["mohr_coulomb_f32c_sym6_2^25"] = {"G_matrices_per_s": A32.shape[0] / tn / 1e6, "ms": tn}
+    del A32, f6, g6
     torch.cuda.empty_cache()
     return paths
 
@@ -503,7 +517,7 @@ def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
 
 
 KERNELS = ("fwd_f64_general9", "bwd_f64_general9", "fwd_f32c_sym6", "bwd_f32c_sym6",
-           "fwd_f64_sym6")
+           "fwd_f64_sym6", "mc_f64_sym6", "mc_f32c_sym6")
 
 
 def run_single(args):
@@ -514,6 +528,18 @@ def run_single(args):
     dev = torch.device("cuda", 0)
     _b.build()
     n = args.n
+    if args.only.startswith("mc_"):
+        prec = "f32c" if "f32c" in args.only else "f64"
+        A = W.stress_field(n, dev, seed=1006).A
+        A = A.float() if prec == "f32c" else A
+        f = torch.empty(n, dtype=A.dtype, device=dev)
+        g = torch.empty_like(A)
+        fn = lambda: eig3.mohr_coulomb(A, precision=prec, grad=True, out=f, grad_out=g)
+        for _ in range(args.warmup):
+            fn()
+        ms = timed(fn, args.steps, torch.cuda.current_stream(dev))
+        print(json.dumps({"kernel": args.only, "n": n, "ms": ms, "G_matrices_per_s": n / ms / 1e6}))
+        return 0
     if "general9" in args.only:
         b = W.workload4(n=n, device=dev)
         A, w = b.A, b.extra["w"]

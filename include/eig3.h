@@ -159,6 +159,33 @@ eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int prec
 eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precision, int64_t n,
                                void *lam, void *P, void *stream);
 
+/*
+ * eig3_mohr_coulomb -- Mohr-Coulomb yield function of the stress tensors
+ * sigma and, optionally, its gradient (Section "Application"):
+ *   f(sigma) = (1/S_yc) ((m+1)/2) max_{i<j} (|s_i - s_j| + K (s_i + s_j)) - 1,
+ *   K = (m-1)/(m+1), s_k the principal stresses (eigenvalues of sigma),
+ *   m = S_yc / S_yt (S_yc, S_yt the uniaxial compressive and tensile yield
+ *   stresses; f = 0 at uniaxial compression -S_yc and tension S_yt).
+ * For m > 0 the maximising pair is always the extreme pair, so with ascending
+ * eigenvalues f = (m lambda_3 - lambda_1) / S_yc - 1; the eigenvalues come
+ * from Algorithm 6 on the stable invariants in the requested precision.
+ * The gradient is the vector-Jacobian product of the eigenvalues with the
+ * weights (-1/S_yc, 0, m/S_yc) (eig3_eigvals_backward's formula and layout
+ * convention: for EIG3_SYM6 it is taken with respect to the six stored
+ * entries, an off-diagonal entry receiving G_ij + G_ji).  Where two computed
+ * eigenvalues coincide exactly their weights are replaced by their mean,
+ * which gives the average of the one-sided gradients -- an element of the
+ * subdifferential of this convex function of a symmetric sigma.  The
+ * eigenvalues and the gradient are computed in one pass per matrix; nothing
+ * but f and grad_sigma is written.
+ *   sigma       device, n matrices (read only).
+ *   s_yc, m     positive finite constants (otherwise EIG3_ERR_ARG).
+ *   f           device, n values of `dtype`.
+ *   grad_sigma  device, n x 9 or n x 6 of `dtype`, or NULL for the value only.
+ */
+eig3_status eig3_mohr_coulomb(const void *sigma, int layout, int dtype, int precision, int64_t n,
+                              double s_yc, double m, void *f, void *grad_sigma, void *stream);
+
 /* Set a device eig3_stats to (0, 0, 0, +inf, 0) on `stream`. */
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream);
 

@@ -22,7 +22,8 @@ from . import _lib
 from ._lib import (F32, F64, GENERAL9, PREC_F32_COMP, PREC_F64, SYM6, Eig3Error, Eig3Stats,
                    check, load)
 
-__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors", "Stats",
+__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors", "mohr_coulomb",
+           "Stats",
            "Eig3Error", "layout_of", "GENERAL9", "SYM6"]
 
 _LAYOUTS = {"general9": GENERAL9, "sym6": SYM6, GENERAL9: GENERAL9, SYM6: SYM6}
@@ -182,6 +183,25 @@ def eigprojectors(A: torch.Tensor, layout=None, precision="f64", return_eigvals=
                                        _ptr(lam), _ptr(P), _stream(dev))
     check(st, "eig3_eigprojectors")
     return (P, lam) if return_eigvals else P
+
+
+def mohr_coulomb(sigma: torch.Tensor, s_yc: float = 100.0, m: float = 10.0, layout=None,
+                 precision="f64", grad=False, out=None, grad_out=None, device=None):
+    """Mohr-Coulomb yield value f(sigma) per stress tensor (n,), and with
+    grad=True also df/dsigma in sigma's storage layout (n, 9) or (n, 6)."""
+    lay = layout_of(sigma, layout)
+    X = _rows(sigma, lay)
+    n = X.shape[0]
+    dev = _device(X, device)
+    f = out if out is not None else _alloc((n,), X.dtype, X, dev)
+    g = None
+    if grad:
+        g = grad_out if grad_out is not None else _alloc(tuple(X.shape), X.dtype, X, dev)
+    with torch.cuda.device(dev):
+        st = load().eig3_mohr_coulomb(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n,
+                                      float(s_yc), float(m), _ptr(f), _ptr(g), _stream(dev))
+    check(st, "eig3_mohr_coulomb")
+    return (f, g) if grad else f
 
 
 class _Eig3Fn(torch.autograd.Function):

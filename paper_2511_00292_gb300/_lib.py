@@ -13,6 +13,7 @@ EXPORTS = (
     "eig3_eigvals",
     "eig3_eigvals_backward",
     "eig3_eigprojectors",
+    "eig3_mohr_coulomb",
     "eig3_stats_reset",
     "eig3_status_string",
     "eig3_version",
@@ -71,6 +72,9 @@ def load():
         lib.eig3_eigvals_backward.restype = I
         lib.eig3_eigprojectors.argtypes = [P, I, I, I, I64, P, P, P]
         lib.eig3_eigprojectors.restype = I
+        lib.eig3_mohr_coulomb.argtypes = [P, I, I, I, I64, ctypes.c_double, ctypes.c_double, P,
+                                          P, P]
+        lib.eig3_mohr_coulomb.restype = I
         lib.eig3_stats_reset.argtypes = [P, P]
         lib.eig3_stats_reset.restype = I
         lib.eig3_status_string.argtypes = [I]

@@ -1,6 +1,7 @@
 // eig3_api.cu -- the library's C ABI (include/eig3.h): host-side argument
 // checks, dispatch to the binary64 or compensated binary32 kernels, launch
 // error reporting, and launch-geometry helpers.
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -156,6 +157,27 @@ eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precisi
   if (precision == EIG3_PREC_F32_COMP)
     return from_cuda(eig3::launch_projectors_f32c(A, layout, n, lam, P, s));
   return from_cuda(eig3::launch_projectors_f64(A, layout, dtype, n, lam, P, s));
+}
+
+eig3_status eig3_mohr_coulomb(const void *sigma, int layout, int dtype, int precision, int64_t n,
+                              double s_yc, double m, void *f, void *grad_sigma, void *stream) {
+  eig3_status st = check_modes(layout, dtype, precision, n);
+  if (st != EIG3_OK) return st;
+  // S_yc and m are positive finite material constants (1/S_yc and m/S_yc
+  // must be finite); checked before anything else is looked at.
+  if (!(s_yc > 0.0) || !(m > 0.0) || !std::isfinite(s_yc) || !std::isfinite(m) ||
+      !std::isfinite(1.0 / s_yc) || !std::isfinite(m / s_yc))
+    return EIG3_ERR_ARG;
+  if (n == 0) return EIG3_OK;
+  if (!sigma || !f) return EIG3_ERR_ARG;
+  const size_t es = elem_size(dtype);
+  if (!aligned(sigma, es) || !aligned(f, es) || (grad_sigma && !aligned(grad_sigma, es)))
+    return EIG3_ERR_ALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == EIG3_PREC_F32_COMP)
+    return from_cuda(eig3::launch_mohr_coulomb_f32c(sigma, layout, n, s_yc, m, f, grad_sigma, s));
+  return from_cuda(
+      eig3::launch_mohr_coulomb_f64(sigma, layout, dtype, n, s_yc, m, f, grad_sigma, s));
 }
 
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream) {

@@ -24,6 +24,8 @@ cudaError_t launch_eigvals_f64(const void *A, int layout, int dtype, int64_t n, 
                                void *aux, eig3_stats *stats, cudaStream_t s);
 cudaError_t launch_projectors_f64(const void *A, int layout, int dtype, int64_t n, void *lam,
                                   void *P, cudaStream_t s);
+cudaError_t launch_mohr_coulomb_f64(const void *A, int layout, int dtype, int64_t n, double s_yc,
+                                    double m, void *f, void *grad_A, cudaStream_t s);
 cudaError_t launch_backward_f64(const void *A, int layout, int dtype, int64_t n,
                                 const void *grad_lam, const void *aux, void *grad_A,
                                 cudaStream_t s);
@@ -35,6 +37,8 @@ cudaError_t launch_eigvals_f32c(const void *A, int layout, int64_t n, void *lam,
                                 eig3_stats *stats, cudaStream_t s);
 cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *lam, void *P,
                                    cudaStream_t s);
+cudaError_t launch_mohr_coulomb_f32c(const void *A, int layout, int64_t n, double s_yc, double m,
+                                     void *f, void *grad_A, cudaStream_t s);
 cudaError_t launch_backward_f32c(const void *A, int layout, int64_t n, const void *grad_lam,
                                  const void *aux, void *grad_A, cudaStream_t s);
 

@@ -29,7 +29,7 @@ def declared_functions():
 def test_header_declares_the_api():
     names = declared_functions()
     for n in ("eig3_invariants", "eig3_eigvals", "eig3_eigvals_backward", "eig3_eigprojectors",
-              "eig3_stats_reset", "eig3_status_string", "eig3_version"):
+              "eig3_mohr_coulomb", "eig3_stats_reset", "eig3_status_string", "eig3_version"):
         assert n in names
 
 
@@ -97,6 +97,17 @@ def test_host_validation_without_gpu(lib):
     assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, None, None) == 1
     assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, bad_ptr, None) == 4
     assert lib.eig3_eigprojectors(ok_ptr, 2, 0, 0, 5, None, ok_ptr, None) == 2
+    # Mohr-Coulomb: material constants are checked first
+    D = ctypes.c_double
+    mc = lib.eig3_mohr_coulomb
+    assert mc(None, 1, 0, 0, 0, D(100.0), D(10.0), None, None, None) == 0
+    for s_yc, m in ((0.0, 10.0), (-1.0, 10.0), (100.0, 0.0), (100.0, -2.0),
+                    (float("nan"), 10.0), (100.0, float("inf")), (1e-320, 10.0)):
+        assert mc(ok_ptr, 1, 0, 0, 5, D(s_yc), D(m), ok_ptr, None, None) == 1, (s_yc, m)
+    assert mc(ok_ptr, 1, 0, 0, 5, D(100.0), D(10.0), None, None, None) == 1
+    assert mc(ok_ptr, 1, 0, 0, 5, D(100.0), D(10.0), ok_ptr, bad_ptr, None) == 4
+    assert mc(ok_ptr, 1, 0, 1, 5, D(100.0), D(10.0), ok_ptr, None, None) == 3
+    assert mc(ok_ptr, 5, 0, 0, 5, D(100.0), D(10.0), ok_ptr, None, None) == 2
     # stats reset
     assert lib.eig3_stats_reset(None, None) == 1
     assert lib.eig3_stats_reset(P(0x10004), None) == 4
