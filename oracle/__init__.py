@@ -13,6 +13,8 @@ Function map (paper sections):
     invariants_naive  Algorithm 3, the naive J3 monomial sum, 4 J2^3 - 27 J3^2
     eigvals           Algorithm 6 on the stable invariants
     eigvals_naive     Algorithm 6 on the naive invariants
+    invariants_naive_tensor / eigvals_naive_tensor
+                      tr(S S)/2 and det S of S = dev(A), then Algorithm 6
     eigvals_grad      d lambda_k / dA = l r^T / (l^T r)  (Section 1, E_k^T)
     eigval_jacobians  the three d lambda_k / dA separately
     mohr_coulomb      the yield function of the application section (+ gradient)
@@ -64,7 +66,8 @@ def _load():
             I = ctypes.c_int
             D = ctypes.c_double
             for name in ("eig3o_invariants_batch", "eig3o_invariants_naive_batch",
-                         "eig3o_eigvals_batch", "eig3o_eigvals_naive_batch"):
+                         "eig3o_invariants_naive_tensor_batch", "eig3o_eigvals_batch",
+                         "eig3o_eigvals_naive_batch", "eig3o_eigvals_naive_tensor_batch"):
                 getattr(lib, name).argtypes = [P, I64, I, P]
                 getattr(lib, name).restype = None
             lib.eig3o_eigvals_grad_batch.argtypes = [P, P, I64, I, P]
@@ -110,6 +113,14 @@ def invariants_naive(X, layout: int = GENERAL9) -> np.ndarray:
     return out
 
 
+def invariants_naive_tensor(X, layout: int = GENERAL9) -> np.ndarray:
+    """(n, 4) array of (I1, J2, J3, Delta) from S = dev(A): tr(S S)/2, det S."""
+    X = _as_input(X, layout)
+    out = np.empty((X.shape[0], 4), dtype=np.float64)
+    _load().eig3o_invariants_naive_tensor_batch(_ptr(X), X.shape[0], layout, _ptr(out))
+    return out
+
+
 def eigvals(X, layout: int = GENERAL9) -> np.ndarray:
     """(n, 3) ascending eigenvalues by Algorithm 6 on the stable invariants."""
     X = _as_input(X, layout)
@@ -123,6 +134,14 @@ def eigvals_naive(X, layout: int = GENERAL9) -> np.ndarray:
     X = _as_input(X, layout)
     out = np.empty((X.shape[0], 3), dtype=np.float64)
     _load().eig3o_eigvals_naive_batch(_ptr(X), X.shape[0], layout, _ptr(out))
+    return out
+
+
+def eigvals_naive_tensor(X, layout: int = GENERAL9) -> np.ndarray:
+    """(n, 3) eigenvalues by Algorithm 6 on the naive tensor invariants."""
+    X = _as_input(X, layout)
+    out = np.empty((X.shape[0], 3), dtype=np.float64)
+    _load().eig3o_eigvals_naive_tensor_batch(_ptr(X), X.shape[0], layout, _ptr(out))
     return out
 
 

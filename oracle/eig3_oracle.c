@@ -205,6 +205,36 @@ void eig3o_invariants_naive(const double *A, double *out) {
 }
 
 /* ---------------------------------------------------------------------- */
+/* comparison: the "naive tensor" invariants of Sections J2, J3 and Delta:  */
+/*   S = A - (tr(A)/3) I,  J2 = tr(S S)/2,  J3 = det S,                     */
+/*   Delta = 4 J2^3 - 27 J3^2.                                              */
+/* tr(S S) = sum_i (S S)_ii with (S S)_ii = sum_k S_ik S_ki (a matrix       */
+/* product and its trace); det S by cofactor expansion along the first     */
+/* row (the paper takes numpy's LU-based determinant here).                */
+/* ---------------------------------------------------------------------- */
+void eig3o_invariants_naive_tensor(const double *A, double *out) {
+  double tr = (A00 + A11) + A22;
+  double m = tr / 3.0;
+  double S[9];
+  for (int j = 0; j < 9; ++j) S[j] = A[j];
+  S[0] = S[0] - m;
+  S[4] = S[4] - m;
+  S[8] = S[8] - m;
+  double t = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double sii = (S[3 * i + 0] * S[0 * 3 + i] + S[3 * i + 1] * S[1 * 3 + i]) + S[3 * i + 2] * S[2 * 3 + i];
+    t = (i == 0) ? sii : t + sii;
+  }
+  double J2 = 0.5 * t;
+  double J3 = S[0] * (S[4] * S[8] - S[5] * S[7]) - S[1] * (S[3] * S[8] - S[5] * S[6]) +
+              S[2] * (S[3] * S[7] - S[4] * S[6]);
+  out[0] = tr;
+  out[1] = J2;
+  out[2] = J3;
+  out[3] = 4.0 * J2 * J2 * J2 - 27.0 * J3 * J3;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Eigenvalue gradient, plain definition (Section 1: E_k^T = d lambda_k/dA).*/
 /* For a simple eigenvalue lambda with right eigenvector r ((A-lambda I)r=0)*/
 /* and left eigenvector l (l^T (A-lambda I) = 0),                          */
@@ -373,6 +403,23 @@ void eig3o_invariants_naive_batch(const double *X, int64_t n, int layout, double
   for (int64_t i = 0; i < n; ++i) {
     load(X, i, layout, A);
     eig3o_invariants_naive(A, out + 4 * i);
+  }
+}
+
+void eig3o_invariants_naive_tensor_batch(const double *X, int64_t n, int layout, double *out) {
+  double A[9];
+  for (int64_t i = 0; i < n; ++i) {
+    load(X, i, layout, A);
+    eig3o_invariants_naive_tensor(A, out + 4 * i);
+  }
+}
+
+void eig3o_eigvals_naive_tensor_batch(const double *X, int64_t n, int layout, double *lam) {
+  double A[9], inv[4];
+  for (int64_t i = 0; i < n; ++i) {
+    load(X, i, layout, A);
+    eig3o_invariants_naive_tensor(A, inv);
+    eig3o_eigvals_from_invariants(inv, lam + 3 * i);
   }
 }
 
