@@ -424,6 +424,27 @@ def measure_paths(eig3, W, dev, stream, steps):
     tq = timed(lambda: eig3.eigprojectors(b3.A, precision="f32c", out=P3), steps, stream)
     paths["eigprojectors_f32c_sym6_2^25"] = {"G_matrices_per_s": b3.n / tq / 1e6, "ms": tq}
     del b3, P3
+    # the paper's comparison variants at scale: time, and distance from the
+    # method's eigenvalues in units of its first-order bound, per spectrum kind
+    b2 = W.workload2(n=1 << 24, device=dev, seed=1102)
+    lv = torch.empty(b2.n, 3, dtype=torch.float64, device=dev)
+    lp = torch.empty_like(lv)
+    bound = b2.kappa * torch.linalg.vector_norm(b2.A, dim=1) * 2.0 ** -53
+    kinds = b2.extra["kinds"]
+    var = {}
+    for v in ("present", "naive", "naive_tensor"):
+        out = lp if v == "present" else lv
+        tv = timed(lambda: eig3.eigvals_variant(b2.A, v, invariants=False, lam_out=out), steps,
+                   stream)
+        var[v] = {"G_matrices_per_s": b2.n / tv / 1e6}
+        if v != "present":
+            r = torch.nan_to_num((lv - lp).abs().amax(dim=1) / bound, nan=float("inf"))
+            for k, name in ((0, "distinct"), (1, "near_double"), (2, "near_triple")):
+                rk = r[kinds == k]
+                var[v][name] = {"max_dist_over_bound": float(rk.amax()),
+                                "frac_beyond_16_bounds": float((rk > 16).float().mean())}
+    paths["variants_f64_general9_2^24"] = var
+    del b2, lv, lp, bound, kinds
     # Mohr-Coulomb yield value + gradient (Section "Application"), fused
     sf = W.stress_field(1 << 25, dev, seed=1006)
     f5 = torch.empty(sf.n, dtype=torch.float64, device=dev)

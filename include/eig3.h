@@ -67,7 +67,9 @@ extern "C" {
 
 typedef enum {
   EIG3_OK = 0,
-  EIG3_ERR_ARG = 1,    /* n < 0, or a required pointer is NULL while n > 0      */
+  EIG3_ERR_ARG = 1,    /* n < 0, a required pointer is NULL while n > 0, or a
+                          scalar argument (material constant, variant) is out
+                          of its range                                           */
   EIG3_ERR_LAYOUT = 2, /* layout is not EIG3_GENERAL9 or EIG3_SYM6              */
   EIG3_ERR_DTYPE = 3,  /* unsupported dtype / precision combination             */
   EIG3_ERR_ALIGN = 4,  /* a pointer is not aligned to its element size          */
@@ -77,6 +79,8 @@ typedef enum {
 enum { EIG3_GENERAL9 = 0, EIG3_SYM6 = 1 };
 enum { EIG3_F64 = 0, EIG3_F32 = 1 };
 enum { EIG3_PREC_F64 = 0, EIG3_PREC_F32_COMP = 1 };
+/* Invariant evaluations of eig3_eigvals_variant (the paper's comparisons). */
+enum { EIG3_VARIANT_PRESENT = 0, EIG3_VARIANT_NAIVE = 1, EIG3_VARIANT_NAIVE_TENSOR = 2 };
 
 /*
  * Per-launch numerical statistics, accumulated on the device by
@@ -185,6 +189,31 @@ eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precisi
  */
 eig3_status eig3_mohr_coulomb(const void *sigma, int layout, int dtype, int precision, int64_t n,
                               double s_yc, double m, void *f, void *grad_sigma, void *stream);
+
+/*
+ * eig3_eigvals_variant -- the invariant evaluations that Sections J2, J3,
+ * Delta and Eigenvalues compare, each followed by Algorithm 6, in binary64
+ * arithmetic, for measuring their stability on large batches.  Not the
+ * method: use eig3_invariants / eig3_eigvals for results.
+ *   variant  EIG3_VARIANT_PRESENT       Algorithms 1, 2, 4, 5 (the values of
+ *                                       eig3_invariants and eig3_eigvals);
+ *            EIG3_VARIANT_NAIVE         Algorithm 3 and the naive J3 monomial
+ *                                       sum, Delta = 4 J2^3 - 27 J3^2;
+ *            EIG3_VARIANT_NAIVE_TENSOR  S = A - tr(A)/3 I, J2 = tr(S S)/2,
+ *                                       J3 = det S (first-row cofactor
+ *                                       expansion), Delta = 4 J2^3 - 27 J3^2.
+ *            Anything else: EIG3_ERR_ARG.
+ *   The naive forms are evaluated as printed, every monomial and sum left
+ *   to right with separately rounded binary64 operations (no FMA), and with
+ *   no scaling, so they over/underflow where the printed formulas do.
+ *   A        device, n matrices (read only); precision is binary64 for every
+ *            dtype.
+ *   inv      device, n x 4 binary64 (I1, J2, J3, Delta), or NULL.
+ *   lam      device, n x 3 of `dtype` (ascending eigenvalues), or NULL.
+ *            At least one of inv and lam is required (else EIG3_ERR_ARG).
+ */
+eig3_status eig3_eigvals_variant(const void *A, int layout, int dtype, int variant, int64_t n,
+                                 double *inv, void *lam, void *stream);
 
 /* Set a device eig3_stats to (0, 0, 0, +inf, 0) on `stream`. */
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream);

@@ -23,6 +23,7 @@ from ._lib import (F32, F64, GENERAL9, PREC_F32_COMP, PREC_F64, SYM6, Eig3Error,
                    check, load)
 
 __all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors", "mohr_coulomb",
+           "eigvals_variant",
            "Stats",
            "Eig3Error", "layout_of", "GENERAL9", "SYM6"]
 
@@ -202,6 +203,32 @@ def mohr_coulomb(sigma: torch.Tensor, s_yc: float = 100.0, m: float = 10.0, layo
                                       float(s_yc), float(m), _ptr(f), _ptr(g), _stream(dev))
     check(st, "eig3_mohr_coulomb")
     return (f, g) if grad else f
+
+
+_VARIANTS = {"present": _lib.VARIANT_PRESENT, "naive": _lib.VARIANT_NAIVE,
+             "naive_tensor": _lib.VARIANT_NAIVE_TENSOR}
+
+
+def eigvals_variant(A: torch.Tensor, variant: str, layout=None, invariants=True, eigvals=True,
+                    inv_out=None, lam_out=None, device=None):
+    """The paper's comparison variants ("naive", "naive_tensor") or the method
+    itself ("present"), binary64 arithmetic: returns (inv (n, 4) or None,
+    lam (n, 3) or None).  For stability measurements, not for results."""
+    lay = layout_of(A, layout)
+    X = _rows(A, lay)
+    n = X.shape[0]
+    dev = _device(X, device)
+    inv = None
+    if invariants:
+        inv = inv_out if inv_out is not None else _alloc((n, 4), torch.float64, X, dev)
+    lam = None
+    if eigvals:
+        lam = lam_out if lam_out is not None else _alloc((n, 3), X.dtype, X, dev)
+    with torch.cuda.device(dev):
+        st = load().eig3_eigvals_variant(_ptr(X), lay, _dtype_code(X), _VARIANTS[variant], n,
+                                         _ptr(inv), _ptr(lam), _stream(dev))
+    check(st, "eig3_eigvals_variant")
+    return inv, lam
 
 
 class _Eig3Fn(torch.autograd.Function):

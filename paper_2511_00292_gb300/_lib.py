@@ -14,6 +14,7 @@ EXPORTS = (
     "eig3_eigvals_backward",
     "eig3_eigprojectors",
     "eig3_mohr_coulomb",
+    "eig3_eigvals_variant",
     "eig3_stats_reset",
     "eig3_status_string",
     "eig3_version",
@@ -22,6 +23,7 @@ EXPORTS = (
 GENERAL9, SYM6 = 0, 1
 F64, F32 = 0, 1
 PREC_F64, PREC_F32_COMP = 0, 1
+VARIANT_PRESENT, VARIANT_NAIVE, VARIANT_NAIVE_TENSOR = 0, 1, 2
 STATUS = {0: "EIG3_OK", 1: "EIG3_ERR_ARG", 2: "EIG3_ERR_LAYOUT", 3: "EIG3_ERR_DTYPE",
           4: "EIG3_ERR_ALIGN", 5: "EIG3_ERR_CUDA"}
 
@@ -75,6 +77,8 @@ def load():
         lib.eig3_mohr_coulomb.argtypes = [P, I, I, I, I64, ctypes.c_double, ctypes.c_double, P,
                                           P, P]
         lib.eig3_mohr_coulomb.restype = I
+        lib.eig3_eigvals_variant.argtypes = [P, I, I, I, I64, P, P, P]
+        lib.eig3_eigvals_variant.restype = I
         lib.eig3_stats_reset.argtypes = [P, P]
         lib.eig3_stats_reset.restype = I
         lib.eig3_status_string.argtypes = [I]

@@ -180,6 +180,22 @@ eig3_status eig3_mohr_coulomb(const void *sigma, int layout, int dtype, int prec
       eig3::launch_mohr_coulomb_f64(sigma, layout, dtype, n, s_yc, m, f, grad_sigma, s));
 }
 
+eig3_status eig3_eigvals_variant(const void *A, int layout, int dtype, int variant, int64_t n,
+                                 double *inv, void *lam, void *stream) {
+  eig3_status st = check_modes(layout, dtype, EIG3_PREC_F64, n);
+  if (st != EIG3_OK) return st;
+  if (variant != EIG3_VARIANT_PRESENT && variant != EIG3_VARIANT_NAIVE &&
+      variant != EIG3_VARIANT_NAIVE_TENSOR)
+    return EIG3_ERR_ARG;
+  if (n == 0) return EIG3_OK;
+  if (!A || (!inv && !lam)) return EIG3_ERR_ARG;
+  const size_t es = elem_size(dtype);
+  if (!aligned(A, es) || (inv && !aligned(inv, 8)) || (lam && !aligned(lam, es)))
+    return EIG3_ERR_ALIGN;
+  return from_cuda(
+      eig3::launch_variant_f64(A, layout, dtype, variant, n, inv, lam, (cudaStream_t)stream));
+}
+
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream) {
   if (!stats) return EIG3_ERR_ARG;
   if (!aligned(stats, 8)) return EIG3_ERR_ALIGN;
@@ -189,7 +205,8 @@ eig3_status eig3_stats_reset(eig3_stats *stats, void *stream) {
 const char *eig3_status_string(int status) {
   switch (status) {
     case EIG3_OK: return "EIG3_OK";
-    case EIG3_ERR_ARG: return "EIG3_ERR_ARG: n < 0 or a required pointer is NULL";
+    case EIG3_ERR_ARG:
+      return "EIG3_ERR_ARG: n < 0, a required pointer is NULL, or a scalar argument is out of range";
     case EIG3_ERR_LAYOUT: return "EIG3_ERR_LAYOUT: layout must be EIG3_GENERAL9 or EIG3_SYM6";
     case EIG3_ERR_DTYPE: return "EIG3_ERR_DTYPE: unsupported dtype/precision combination";
     case EIG3_ERR_ALIGN: return "EIG3_ERR_ALIGN: pointer not aligned to its element size";

@@ -26,30 +26,6 @@ struct Rows {
   static constexpr int N = (LAYOUT == EIG3_GENERAL9) ? 9 : 6;
 };
 
-// Walks the batch in tiles of kTile rows (grid-stride over tiles), the next
-// tile's rows copied into shared memory while the current one is computed;
-// calls body(row_index, values) for every row.
-template <int N, typename T, typename Body>
-__device__ __forceinline__ void for_each_row(const T *__restrict__ A, int64_t n, T (*sA)[kTile * N],
-                                             Body body) {
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles)
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();  // tile t is in sA[buf]; every thread is done with sA[buf ^ 1]
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) body(t * kTile + threadIdx.x, &sA[buf][threadIdx.x * N]);
-    buf ^= 1;
-  }
-}
-
 // binary64 arithmetic; c1 = 1/S_yc, cm = m/S_yc
 template <int LAYOUT, typename T, bool GRAD>
 __global__ void __launch_bounds__(kThreads)

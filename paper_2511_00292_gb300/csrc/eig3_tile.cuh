@@ -57,4 +57,29 @@ __device__ __forceinline__ void tile_issue(const E *__restrict__ g, int64_t e0, 
   for (int i = head + threadIdx.x; i < count; i += blockDim.x) s[i] = __ldg(src + i);
 }
 
+// The loop above as one call: walks the batch of n rows of N elements in
+// tiles (grid-stride over tiles, the next tile staged while the current one
+// is computed) and calls body(row_index, row) for every row, with row
+// pointing into shared memory.  sA holds two tiles.
+template <int N, typename T, typename Body>
+__device__ __forceinline__ void for_each_row(const T *__restrict__ A, int64_t n, T (*sA)[kTile * N],
+                                             Body body) {
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles)
+    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int rows = rows_of(t);
+    cp_async_wait_all();
+    __syncthreads();  // tile t is in sA[buf]; every thread is done with sA[buf ^ 1]
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
+    cp_async_commit();
+    if ((int)threadIdx.x < rows) body(t * kTile + threadIdx.x, &sA[buf][threadIdx.x * N]);
+    buf ^= 1;
+  }
+}
+
 }  // namespace eig3

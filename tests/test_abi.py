@@ -29,7 +29,8 @@ def declared_functions():
 def test_header_declares_the_api():
     names = declared_functions()
     for n in ("eig3_invariants", "eig3_eigvals", "eig3_eigvals_backward", "eig3_eigprojectors",
-              "eig3_mohr_coulomb", "eig3_stats_reset", "eig3_status_string", "eig3_version"):
+              "eig3_mohr_coulomb", "eig3_eigvals_variant", "eig3_stats_reset",
+              "eig3_status_string", "eig3_version"):
         assert n in names
 
 
@@ -108,6 +109,17 @@ def test_host_validation_without_gpu(lib):
     assert mc(ok_ptr, 1, 0, 0, 5, D(100.0), D(10.0), ok_ptr, bad_ptr, None) == 4
     assert mc(ok_ptr, 1, 0, 1, 5, D(100.0), D(10.0), ok_ptr, None, None) == 3
     assert mc(ok_ptr, 5, 0, 0, 5, D(100.0), D(10.0), ok_ptr, None, None) == 2
+    # comparison variants
+    var = lib.eig3_eigvals_variant
+    assert var(None, 0, 0, 1, 0, None, None, None) == 0
+    assert var(ok_ptr, 0, 0, 3, 5, ok_ptr, None, None) == 1          # unknown variant
+    assert var(ok_ptr, 0, 0, -1, 5, ok_ptr, None, None) == 1
+    assert var(ok_ptr, 0, 0, 1, 5, None, None, None) == 1            # no output at all
+    assert var(None, 0, 0, 1, 5, ok_ptr, None, None) == 1
+    assert var(ok_ptr, 0, 0, 1, 5, P(0x10004), None, None) == 4      # inv is binary64
+    assert var(ok_ptr, 0, 1, 2, 5, None, P(0x10002), None) == 4
+    assert var(ok_ptr, 3, 0, 1, 5, ok_ptr, None, None) == 2
+    assert var(ok_ptr, 0, 2, 1, 5, ok_ptr, None, None) == 3
     # stats reset
     assert lib.eig3_stats_reset(None, None) == 1
     assert lib.eig3_stats_reset(P(0x10004), None) == 4
