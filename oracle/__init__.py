@@ -20,6 +20,9 @@ Function map (paper sections):
     mohr_coulomb      the yield function of the application section (+ gradient)
     bounds            first-order stability bounds, C = 1, Frobenius norm
     eigvals_mt        eigvals on POSIX threads, for timing on host cores
+    eigvals_exact     (oracle/exact.py) the exact eigenvalues of the stored
+                      matrix: roots of its exact characteristic polynomial,
+                      the reference the stability bounds are stated against
 """
 from __future__ import annotations
 
@@ -209,3 +212,6 @@ def sym6_to_general9(S) -> np.ndarray:
     A[:, 3] = S[:, 5]; A[:, 4] = S[:, 1]; A[:, 5] = S[:, 3]
     A[:, 6] = S[:, 4]; A[:, 7] = S[:, 3]; A[:, 8] = S[:, 2]
     return A
+
+
+from .exact import eigvals_exact  # noqa: E402  (pure Python, no compiled part)

@@ -242,6 +242,32 @@ def workload2(n: int = 1 << 26, device="cpu", seed: int = 1002, chunk: int = 1 <
     return Batch(A, "general9", kappa, lam, dict(kinds=kinds))
 
 
+def illconditioned(n: int, device="cpu", seed: int = 1007, log10_kappa_max: float = 4.0,
+                   chunk: int = 1 << 22) -> Batch:
+    """General FP64 matrices with ill-conditioned eigenbases: V = Q1 diag(s) Q2
+    with s = (1, 10^(t u), 10^t), t ~ U[0, log10_kappa_max], u ~ U[0, 1], so
+    kappa_2(V) = 10^t; spectra one third each distinct / double / triple with
+    delta log-uniform in [1e-12, 1e-2] (the paper's U2(1e-3) has kappa ~ 9e3)."""
+    g = _gen(seed, device)
+    A = torch.empty((n, 9), dtype=torch.float64, device=device)
+    kappa = torch.empty(n, dtype=torch.float64, device=device)
+    lam = torch.empty((n, 3), dtype=torch.float64, device=device)
+    kinds = torch.empty(n, dtype=torch.int64, device=device)
+    for i, m in _chunks(n, chunk):
+        Q1 = haar_o3(m, g, device)
+        Q2 = haar_o3(m, g, device)
+        t = uniform(m, 0.0, log10_kappa_max, g, device)
+        u = torch.rand(m, generator=g, device=device, dtype=torch.float64)
+        sv = torch.stack([torch.ones_like(t), torch.pow(10.0, t * u), torch.pow(10.0, t)], dim=1)
+        kd = torch.randint(0, 3, (m,), generator=g, device=device)
+        lm = spectra(m, kd, 1e-12, 1e-2, g, device)
+        A[i:i + m] = general_from_spectrum(lm, Q1, sv, Q2).reshape(m, 9)
+        kappa[i:i + m] = torch.pow(10.0, t)
+        lam[i:i + m] = lm
+        kinds[i:i + m] = kd
+    return Batch(A, "general9", kappa, lam, dict(kinds=kinds))
+
+
 def workload3(n: int = 1 << 27, device="cpu", seed: int = 1003, chunk: int = 1 << 22) -> Batch:
     """Workload 3: symmetric 6-entry FP32 stress field."""
     g = _gen(seed, device)
