@@ -445,6 +445,24 @@ def measure_paths(eig3, W, dev, stream, steps):
                                 "frac_beyond_16_bounds": float((rk > 16).float().mean())}
     paths["variants_f64_general9_2^24"] = var
     del b2, lv, lp, bound, kinds
+    # the guarded binary64 precision: cost on well-conditioned general matrices
+    # (workload 2) and on ill-conditioned ones (kappa up to 1e4), with the
+    # share of matrices the guard switched to the QR algorithm
+    guard = {}
+    for name, bt in (("workload2_2^24", W.workload2(n=1 << 24, device=dev, seed=1103)),
+                     ("ill_conditioned_kappa_le_1e4_2^24",
+                      W.illconditioned(1 << 24, dev, seed=1104, log10_kappa_max=4.0))):
+        lg = torch.empty(bt.n, 3, dtype=torch.float64, device=dev)
+        lpl = torch.empty_like(lg)
+        st = eig3.Stats(dev)
+        tg = timed(lambda: eig3.eigvals(bt.A, precision="f64g", out=lg), steps, stream)
+        tp = timed(lambda: eig3.eigvals(bt.A, out=lpl), steps, stream)
+        eig3.eigvals(bt.A, precision="f64g", out=lg, stats=st)
+        guard[name] = {"f64g_G_matrices_per_s": bt.n / tg / 1e6,
+                       "f64_G_matrices_per_s": bt.n / tp / 1e6,
+                       "switched_fraction": st.read()["n_guarded"] / bt.n}
+        del bt, lg, lpl
+    paths["guarded_f64_general9"] = guard
     # Mohr-Coulomb yield value + gradient (Section "Application"), fused
     sf = W.stress_field(1 << 25, dev, seed=1006)
     f5 = torch.empty(sf.n, dtype=torch.float64, device=dev)

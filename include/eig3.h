@@ -46,6 +46,22 @@
  *                                  arithmetic on this path except the binary64
  *                                  invariants output of eig3_invariants.
  *  EIG3_F64 + EIG3_PREC_F32_COMP   rejected with EIG3_ERR_DTYPE.
+ *  EIG3_F64/F32 + EIG3_PREC_F64_GUARDED
+ *                                  binary64 arithmetic with a guard for
+ *                                  ill-conditioned eigenbases (where Sections
+ *                                  J3, Delta and Eigenvalues find Algorithms 4
+ *                                  and 5 lose accuracy and an iterative method
+ *                                  does not): a general matrix whose deviatoric
+ *                                  part S is far from normal, ||S||_F^2 >
+ *                                  32 tr(S^2), gets its eigenvalues from the
+ *                                  shifted QR algorithm on the 3x3 matrix
+ *                                  (backward stable, at most 64 steps); every
+ *                                  other matrix gets exactly the
+ *                                  EIG3_PREC_F64 results.  Symmetric input
+ *                                  (normal) is never switched.  Accepted by
+ *                                  eig3_eigvals and eig3_eigvals_backward;
+ *                                  the other entry points reject it with
+ *                                  EIG3_ERR_DTYPE.
  *
  * Readings of the paper built into the library
  *  - Algorithm 5, term r10: +M02*M21*d2 (the printed minus sign does not
@@ -78,14 +94,14 @@ typedef enum {
 
 enum { EIG3_GENERAL9 = 0, EIG3_SYM6 = 1 };
 enum { EIG3_F64 = 0, EIG3_F32 = 1 };
-enum { EIG3_PREC_F64 = 0, EIG3_PREC_F32_COMP = 1 };
+enum { EIG3_PREC_F64 = 0, EIG3_PREC_F32_COMP = 1, EIG3_PREC_F64_GUARDED = 2 };
 /* Invariant evaluations of eig3_eigvals_variant (the paper's comparisons). */
 enum { EIG3_VARIANT_PRESENT = 0, EIG3_VARIANT_NAIVE = 1, EIG3_VARIANT_NAIVE_TENSOR = 2 };
 
 /*
  * Per-launch numerical statistics, accumulated on the device by
  * eig3_eigvals when a non-NULL device pointer is passed.  Reset it with
- * eig3_stats_reset before the first accumulating call.  40 bytes, 8-aligned.
+ * eig3_stats_reset before the first accumulating call.  48 bytes, 8-aligned.
  * Several calls may accumulate into one struct (counts add, min/max combine).
  */
 typedef struct {
@@ -97,6 +113,8 @@ typedef struct {
                                          (0 at a repeated eigenvalue); evaluated in
                                          binary32 from the computed triple angle */
   double max_abs_lambda;              /* max over matrices of max_k |lambda_k|      */
+  unsigned long long n_guarded;       /* matrices EIG3_PREC_F64_GUARDED switched to
+                                         the QR algorithm                           */
 } eig3_stats;
 
 /*
@@ -215,7 +233,7 @@ eig3_status eig3_mohr_coulomb(const void *sigma, int layout, int dtype, int prec
 eig3_status eig3_eigvals_variant(const void *A, int layout, int dtype, int variant, int64_t n,
                                  double *inv, void *lam, void *stream);
 
-/* Set a device eig3_stats to (0, 0, 0, +inf, 0) on `stream`. */
+/* Set a device eig3_stats to (0, 0, 0, +inf, 0, 0) on `stream`. */
 eig3_status eig3_stats_reset(eig3_stats *stats, void *stream);
 
 /* Human-readable name of a status code (static string). */

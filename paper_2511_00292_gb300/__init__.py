@@ -9,8 +9,10 @@ write directly over the host link (zero copy), and the library must be built.
 
 Layouts: ``"general9"`` (n, 9) row-major, or (n, 3, 3); ``"sym6"`` (n, 6) in
 the order (A00, A11, A22, A12, A02, A01).
-Precisions: ``"f64"`` (binary64 arithmetic; storage float64 or float32) and
-``"f32c"`` (compensated binary32 arithmetic; storage float32).
+Precisions: ``"f64"`` (binary64 arithmetic; storage float64 or float32),
+``"f32c"`` (compensated binary32 arithmetic; storage float32) and ``"f64g"``
+(binary64 with the guard for ill-conditioned eigenbases: strongly non-normal
+matrices get compensated binary64 invariants).
 """
 from __future__ import annotations
 
@@ -28,8 +30,9 @@ __all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojec
            "Eig3Error", "layout_of", "GENERAL9", "SYM6"]
 
 _LAYOUTS = {"general9": GENERAL9, "sym6": SYM6, GENERAL9: GENERAL9, SYM6: SYM6}
-_PRECS = {"f64": PREC_F64, "f32c": PREC_F32_COMP, PREC_F64: PREC_F64,
-          PREC_F32_COMP: PREC_F32_COMP}
+_PRECS = {"f64": PREC_F64, "f32c": PREC_F32_COMP, "f64g": _lib.PREC_F64_GUARDED,
+          PREC_F64: PREC_F64, PREC_F32_COMP: PREC_F32_COMP,
+          _lib.PREC_F64_GUARDED: _lib.PREC_F64_GUARDED}
 
 
 def layout_of(A: torch.Tensor, layout=None) -> int:
@@ -92,7 +95,7 @@ class Stats:
     """Device-resident eig3_stats accumulated by :func:`eigvals` (see eig3.h)."""
 
     def __init__(self, device=None):
-        self.buf = torch.empty(5, dtype=torch.float64,
+        self.buf = torch.empty(6, dtype=torch.float64,
                                device=device if device is not None else torch.device("cuda"))
         self.reset()
 

@@ -22,20 +22,21 @@ EXPORTS = (
 
 GENERAL9, SYM6 = 0, 1
 F64, F32 = 0, 1
-PREC_F64, PREC_F32_COMP = 0, 1
+PREC_F64, PREC_F32_COMP, PREC_F64_GUARDED = 0, 1, 2
 VARIANT_PRESENT, VARIANT_NAIVE, VARIANT_NAIVE_TENSOR = 0, 1, 2
 STATUS = {0: "EIG3_OK", 1: "EIG3_ERR_ARG", 2: "EIG3_ERR_LAYOUT", 3: "EIG3_ERR_DTYPE",
           4: "EIG3_ERR_ALIGN", 5: "EIG3_ERR_CUDA"}
 
 
 class Eig3Stats(ctypes.Structure):
-    """Mirror of eig3_stats (40 bytes)."""
+    """Mirror of eig3_stats (48 bytes)."""
     _fields_ = [
         ("n_delta_clamped", ctypes.c_ulonglong),
         ("n_j2_clamped", ctypes.c_ulonglong),
         ("n_nonfinite", ctypes.c_ulonglong),
         ("min_disc_ratio", ctypes.c_double),
         ("max_abs_lambda", ctypes.c_double),
+        ("n_guarded", ctypes.c_ulonglong),
     ]
 
 

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libeig3.so")
 
-UNITS = ["eig3_api.cu", "eig3_f64.cu", "eig3_f32c.cu", "eig3_mohr_coulomb.cu", "eig3_variants.cu"]
+UNITS = ["eig3_api.cu", "eig3_f64.cu", "eig3_f32c.cu", "eig3_mohr_coulomb.cu", "eig3_variants.cu",
+         "eig3_guard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
           "-I", INCLUDE, "-I", CSRC]

@@ -44,6 +44,12 @@ cudaError_t launch_mohr_coulomb_f32c(const void *A, int layout, int64_t n, doubl
 cudaError_t launch_backward_f32c(const void *A, int layout, int64_t n, const void *grad_lam,
                                  const void *aux, void *grad_A, cudaStream_t s);
 
+// binary64 with the guard for ill-conditioned eigenbases, general 9-entry layout
+cudaError_t launch_eigvals_guarded(const void *A, int dtype, int64_t n, void *lam, void *aux,
+                                   eig3_stats *stats, cudaStream_t s);
+cudaError_t launch_backward_guarded(const void *A, int dtype, int64_t n, const void *grad_lam,
+                                    void *grad_A, cudaStream_t s);
+
 cudaError_t launch_stats_reset(eig3_stats *stats, cudaStream_t s);
 
 }  // namespace eig3

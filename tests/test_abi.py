@@ -49,7 +49,7 @@ def test_library_is_sm_103a_and_static_runtime():
 
 
 def test_version_and_status_strings(lib):
-    assert lib.eig3_version() == 10000
+    assert lib.eig3_version() == 10100
     assert lib.eig3_status_string(0) == b"EIG3_OK"
     for code in range(1, 6):
         assert lib.eig3_status_string(code).startswith(b"EIG3_ERR")
@@ -58,7 +58,7 @@ def test_version_and_status_strings(lib):
 
 def test_stats_struct_layout():
     from paper_2511_00292_gb300._lib import Eig3Stats
-    assert ctypes.sizeof(Eig3Stats) == 40
+    assert ctypes.sizeof(Eig3Stats) == 48
 
 
 P = ctypes.c_void_p
@@ -98,6 +98,13 @@ def test_host_validation_without_gpu(lib):
     assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, None, None) == 1
     assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, bad_ptr, None) == 4
     assert lib.eig3_eigprojectors(ok_ptr, 2, 0, 0, 5, None, ok_ptr, None) == 2
+    # the guarded precision: eigenvalues and adjoint only
+    assert lib.eig3_eigvals(ok_ptr, 0, 0, 3, 5, ok_ptr, None, None, None) == 3   # unknown
+    assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 2, 5, None, ok_ptr, None) == 3
+    assert lib.eig3_invariants(ok_ptr, 0, 0, 2, 5, ok_ptr, None) == 3
+    assert lib.eig3_mohr_coulomb(ok_ptr, 1, 0, 2, 5, ctypes.c_double(100.0),
+                                 ctypes.c_double(10.0), ok_ptr, None, None) == 3
+    assert lib.eig3_eigvals(bad_ptr, 0, 0, 2, 5, ok_ptr, None, None, None) == 4
     # Mohr-Coulomb: material constants are checked first
     D = ctypes.c_double
     mc = lib.eig3_mohr_coulomb
