@@ -498,11 +498,10 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
     ogG = torch.empty_like(hG).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
     d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
-    pipe = HostPipeline(dev, chunk=1 << 24, depth=2)
+    pipe = HostPipeline(dev, chunk=1 << 22, depth=3)
 
     def step():
-        pipe.forward_backward(hS, hwS, olS, ogS, precision="f32c")
-        pipe.forward_backward(hG, hwG, olG, ogG, precision="f64")
+        pipe.run([(hS, hwS, olS, ogS, None, "f32c"), (hG, hwG, olG, ogG, None, "f64")])
 
     step()
     torch.cuda.synchronize(dev)
@@ -513,7 +512,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
         bool(torch.equal(olS[:1024], eig3.eigvals(S.A[:1024], precision="f32c").cpu()))
     del hS, hG, hwS, hwG, olS, olG, ogS, ogG, pipe
     return {"value": (S.n + G.n) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "mode": "pinned host buffers, chunks of 2^24 streamed through 2 device slots "
+            "mode": "pinned host buffers, chunks of 2^22 streamed through 3 device slots "
                     "(H2D / kernels / D2H on 3 streams)",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
             "results_match_device": ok}

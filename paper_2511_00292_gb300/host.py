@@ -4,7 +4,10 @@ For a batch that lives in page-locked host memory, `HostPipeline` runs the
 library's forward and adjoint on fixed-size chunks with three CUDA streams:
 host-to-device copies of chunk i+1, the kernels on chunk i and the
 device-to-host copies of chunk i-1 overlap, so the step costs about the
-slowest of the three instead of their sum.  The device slots are allocated
+slowest of the three instead of their sum.  The three stages touch three
+different device slots, so the default depth is 3 (with 2, the copy of chunk
+i+1 would wait for the copy-back of chunk i-1 from the same slot and the two
+copy directions would not overlap).  The device slots are allocated
 once per pipeline with torch (plumbing; the kernels only see their inputs and
 outputs).  Every computation is a call of the C ABI.
 """
@@ -16,7 +19,7 @@ from . import eigvals, eigvals_backward, layout_of
 
 
 class HostPipeline:
-    def __init__(self, device=None, chunk: int = 1 << 24, depth: int = 2):
+    def __init__(self, device=None, chunk: int = 1 << 24, depth: int = 3):
         self.dev = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self.chunk = int(chunk)
@@ -42,37 +45,50 @@ class HostPipeline:
         gradient of sum(w * lambda) into grad_out (both pinned host tensors).
         Asynchronous with respect to the host; ordered after the current stream's
         pending work, and the current stream waits for the last copy."""
-        for t in (A, w, lam_out, grad_out):
-            if t.is_cuda or not t.is_pinned():
-                raise ValueError("HostPipeline works on pinned host tensors")
-        lay = layout_of(A, layout)
-        width = 9 if lay == 0 else 6
-        X = A.reshape(-1, width)
-        n = X.shape[0]
-        slots = self._get_slots((width, A.dtype), width, A.dtype)
+        self.run([(A, w, lam_out, grad_out, layout, precision)])
+
+    def run(self, jobs):
+        """Several forward_backward jobs, (A, w, lam_out, grad_out, layout,
+        precision) each, streamed back to back: the chunks of the next job enter
+        the pipeline while the last ones of the previous job are still in it."""
+        for job in jobs:
+            for t in job[:4]:
+                if t.is_cuda or not t.is_pinned():
+                    raise ValueError("HostPipeline works on pinned host tensors")
         main = torch.cuda.current_stream(self.dev)
         for s in (self.s_in, self.s_run, self.s_out):
             s.wait_stream(main)
-        for i, lo in enumerate(range(0, n, self.chunk)):
-            hi = min(n, lo + self.chunk)
-            m = hi - lo
-            k = i % self.depth
-            dA, dw = slots["A"][k][:m], slots["w"][k][:m]
-            dl, da, dg = slots["lam"][k][:m], slots["aux"][k][:m], slots["g"][k][:m]
-            with torch.cuda.stream(self.s_in):
-                if i >= self.depth:
-                    self.s_in.wait_event(slots["free"][k])
-                dA.copy_(X[lo:hi], non_blocking=True)
-                dw.copy_(w[lo:hi], non_blocking=True)
-                slots["loaded"][k].record(self.s_in)
-            with torch.cuda.stream(self.s_run):
-                self.s_run.wait_event(slots["loaded"][k])
-                eigvals(dA, layout=lay, precision=precision, return_aux=True, out=dl, aux_out=da)
-                eigvals_backward(dA, dw, aux=da, layout=lay, precision=precision, out=dg)
-                slots["done"][k].record(self.s_run)
-            with torch.cuda.stream(self.s_out):
-                self.s_out.wait_event(slots["done"][k])
-                lam_out[lo:hi].copy_(dl, non_blocking=True)
-                grad_out.reshape(-1, width)[lo:hi].copy_(dg, non_blocking=True)
-                slots["free"][k].record(self.s_out)
+        used = {}  # chunks issued per slot set in this run
+        for A, w, lam_out, grad_out, layout, precision in jobs:
+            lay = layout_of(A, layout)
+            width = 9 if lay == 0 else 6
+            X = A.reshape(-1, width)
+            n = X.shape[0]
+            key = (width, A.dtype)
+            slots = self._get_slots(key, width, A.dtype)
+            for lo in range(0, n, self.chunk):
+                i = used.get(key, 0)
+                used[key] = i + 1
+                hi = min(n, lo + self.chunk)
+                m = hi - lo
+                k = i % self.depth
+                dA, dw = slots["A"][k][:m], slots["w"][k][:m]
+                dl, da, dg = slots["lam"][k][:m], slots["aux"][k][:m], slots["g"][k][:m]
+                with torch.cuda.stream(self.s_in):
+                    if i >= self.depth:
+                        self.s_in.wait_event(slots["free"][k])
+                    dA.copy_(X[lo:hi], non_blocking=True)
+                    dw.copy_(w[lo:hi], non_blocking=True)
+                    slots["loaded"][k].record(self.s_in)
+                with torch.cuda.stream(self.s_run):
+                    self.s_run.wait_event(slots["loaded"][k])
+                    eigvals(dA, layout=lay, precision=precision, return_aux=True, out=dl,
+                            aux_out=da)
+                    eigvals_backward(dA, dw, aux=da, layout=lay, precision=precision, out=dg)
+                    slots["done"][k].record(self.s_run)
+                with torch.cuda.stream(self.s_out):
+                    self.s_out.wait_event(slots["done"][k])
+                    lam_out[lo:hi].copy_(dl, non_blocking=True)
+                    grad_out.reshape(-1, width)[lo:hi].copy_(dg, non_blocking=True)
+                    slots["free"][k].record(self.s_out)
         main.wait_stream(self.s_out)

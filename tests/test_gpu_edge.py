@@ -282,7 +282,8 @@ def test_zero_copy_pinned_host_buffers(eig3):
         eig3.eigvals(bt.A)          # pageable host memory is refused
 
 
-def test_host_pipeline_matches_device(eig3):
+@pytest.mark.parametrize("depth", [2, 3])
+def test_host_pipeline_matches_device(eig3, depth):
     """Chunked host-to-device streaming gives the device results bit for bit,
     including a ragged last chunk and more chunks than device slots."""
     from paper_2511_00292_gb300.host import HostPipeline
@@ -290,7 +291,7 @@ def test_host_pipeline_matches_device(eig3):
     hA, hw = bt.A.pin_memory(), bt.extra["w"].pin_memory()
     lam = torch.empty(bt.n, 3, dtype=torch.float64).pin_memory()
     grad = torch.empty_like(hA).pin_memory()
-    pipe = HostPipeline(dev(), chunk=1024, depth=2)
+    pipe = HostPipeline(dev(), chunk=1024, depth=depth)
     pipe.forward_backward(hA, hw, lam, grad)
     torch.cuda.synchronize()
     dA = bt.A.to(dev())
