@@ -92,3 +92,15 @@ class HostPipeline:
                     grad_out.reshape(-1, width)[lo:hi].copy_(dg, non_blocking=True)
                     slots["free"][k].record(self.s_out)
         main.wait_stream(self.s_out)
+
+    def capture(self, jobs) -> torch.cuda.CUDAGraph:
+        """run(jobs) captured once into a CUDA graph (copies, kernels and the
+        cross-stream dependencies); each replay() repeats the whole run on the
+        same host and device buffers with a single launch from the host."""
+        self.run(jobs)  # allocates the device slots and loads the library
+        torch.cuda.synchronize(self.dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(jobs)
+        return g
+

@@ -307,3 +307,30 @@ def test_host_pipeline_matches_device(eig3, depth):
     l2, a2 = eig3.eigvals(S.to(dev()), precision="f32c", return_aux=True)
     g2 = eig3.eigvals_backward(S.to(dev()), wS.to(dev()), aux=a2, precision="f32c")
     assert torch.equal(lS, l2.cpu()) and torch.equal(gS, g2.cpu())
+
+
+def test_host_pipeline_graph_replay(eig3):
+    """The captured pipeline (one graph launch per step) gives the results of
+    the direct run bit for bit, replay after replay, with both jobs in it."""
+    from paper_2511_00292_gb300.host import HostPipeline
+    bt = W.workload4(n=9_001, device="cpu", seed=2202)
+    S = W.workload3(n=7_003, device="cpu", seed=2203).A
+    wS = torch.randn(S.shape[0], 3, dtype=torch.float32)
+    hA, hw, hS, hwS = (t.pin_memory() for t in (bt.A, bt.extra["w"], S, wS))
+    outs = [torch.empty(bt.n, 3, dtype=torch.float64).pin_memory(),
+            torch.empty_like(hA).pin_memory(),
+            torch.empty(S.shape[0], 3, dtype=torch.float32).pin_memory(),
+            torch.empty_like(hS).pin_memory()]
+    jobs = [(hS, hwS, outs[2], outs[3], None, "f32c"), (hA, hw, outs[0], outs[1], None, "f64")]
+    pipe = HostPipeline(dev(), chunk=2048, depth=3)
+    pipe.run(jobs)
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    g = pipe.capture(jobs)
+    for o in outs:
+        o.zero_()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert all(torch.equal(o, r) for o, r in zip(outs, ref))
+
