@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(kThreads)
                    float *__restrict__ P) {
   constexpr int N = WidthC<LAYOUT>::N;
   __shared__ __align__(16) float sA[2][kTile * N];
+  // the tile's outputs, written back coalesced (27 floats per row: a 108-byte
+  // stride between lanes when stored directly)
+  __shared__ __align__(16) float sP[kTile * 27];
+  __shared__ __align__(16) float sL[LAM ? kTile * 3 : 4];
   const int64_t ntiles = (n + kTile - 1) / kTile;
   auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
   int buf = 0;
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t r0 = t * kTile;
     const int rows = rows_of(t);
     cp_async_wait_all();
-    __syncthreads();
+    __syncthreads();  // also: every thread is done storing the previous tile's outputs
     const int64_t tn = t + gridDim.x;
     if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
     cp_async_commit();
@@ -206,18 +210,20 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
       const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
-      const int64_t i = r0 + threadIdx.x;
       if constexpr (LAM) {
-        lam[3 * i + 0] = e.l1;
-        lam[3 * i + 1] = e.l2;
-        lam[3 * i + 2] = e.l3;
+        sL[3 * threadIdx.x + 0] = e.l1;
+        sL[3 * threadIdx.x + 1] = e.l2;
+        sL[3 * threadIdx.x + 2] = e.l3;
       }
       float E[27];
       projectors_c<N>(a, adjoint_units_c(e.r, e.sigma1, e.sigma2), E);
-      float *q = P + 27 * i;
+      float *q = sP + 27 * threadIdx.x;
 #pragma unroll
       for (int j = 0; j < 27; ++j) q[j] = E[j];
     }
+    __syncthreads();
+    tile_store(sP, rows * 27, P, r0 * 27);
+    if constexpr (LAM) tile_store(sL, rows * 3, lam, r0 * 3);
     buf ^= 1;
   }
 }

@@ -57,6 +57,27 @@ __device__ __forceinline__ void tile_issue(const E *__restrict__ g, int64_t e0, 
   for (int i = head + threadIdx.x; i < count; i += blockDim.x) s[i] = __ldg(src + i);
 }
 
+// Store count elements s[0 .. count) (shared memory, 16-byte aligned) to
+// g[e0 .. e0+count) cooperatively: 16-byte vector stores when the destination
+// is 16-byte aligned, element stores for the rest.  Rows that are produced
+// one per thread and are longer than a few elements (e.g. 27 projector
+// entries) are written coalesced this way instead of with a 108-byte stride
+// between the lanes of a warp.
+template <typename E>
+__device__ __forceinline__ void tile_store(const E *__restrict__ s, int count,
+                                           E *__restrict__ g, int64_t e0) {
+  E *dst = g + e0;
+  int head = 0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+    const int n16 = (count * (int)sizeof(E)) >> 4;
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) d4[i] = s4[i];
+    head = (n16 << 4) / (int)sizeof(E);
+  }
+  for (int i = head + threadIdx.x; i < count; i += blockDim.x) dst[i] = s[i];
+}
+
 // The loop above as one call: walks the batch of n rows of N elements in
 // tiles (grid-stride over tiles, the next tile staged while the current one
 // is computed) and calls body(row_index, row) for every row, with row

@@ -149,3 +149,26 @@ def test_projectors_f32c(eig3):
     tol = 64 * U.U32 / gap[sel]
     print(f"[proj] f32c n={sel.sum()} max err/tol {np.max(err / tol):.3g}")
     assert np.all(err <= tol)
+
+
+@pytest.mark.parametrize("layout", ["sym6", "general9"])
+def test_projectors_f32c_output_alignment_and_ragged_tiles(eig3, layout):
+    """The binary32 kernel writes each tile's outputs back through shared
+    memory: with 16-byte stores when the output is 16-byte aligned, element
+    stores otherwise.  Both give the same bytes, for every tile size."""
+    S = W.workload3(n=3 * 256 + 77, device="cpu", seed=2303).A
+    X = S if layout == "sym6" else torch.as_tensor(oracle.sym6_to_general9(S.double().numpy()),
+                                                    dtype=torch.float32)
+    Xd = X.to(dev())
+    n = Xd.shape[0]
+    P, lam = eig3.eigprojectors(Xd, layout=layout, precision="f32c", return_eigvals=True)
+    bufP = torch.full((n * 27 + 1,), float("nan"), dtype=torch.float32, device=dev())
+    bufL = torch.full((n * 3 + 1,), float("nan"), dtype=torch.float32, device=dev())
+    P1, lam1 = eig3.eigprojectors(Xd, layout=layout, precision="f32c", return_eigvals=True,
+                                  out=bufP[1:].view(n, 3, 3, 3), lam_out=bufL[1:].view(n, 3))
+    assert torch.equal(P, P1) and torch.equal(lam, lam1)
+    assert torch.isnan(bufP[0]) and torch.isnan(bufL[0])
+    assert torch.equal(lam, eig3.eigvals(Xd, layout=layout, precision="f32c"))
+    for m in (1, 255, 256, 257):
+        Pm = eig3.eigprojectors(Xd[:m], layout=layout, precision="f32c")
+        assert torch.equal(Pm, P[:m])
