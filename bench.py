@@ -568,7 +568,8 @@ def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
 
 
 KERNELS = ("fwd_f64_general9", "bwd_f64_general9", "fwd_f32c_sym6", "bwd_f32c_sym6",
-           "fwd_f64_sym6", "mc_f64_sym6", "mc_f32c_sym6")
+           "fwd_f64_sym6", "mc_f64_sym6", "mc_f32c_sym6", "guard_f64_illcond",
+           "proj_f32c_sym6")
 
 
 def run_single(args):
@@ -579,6 +580,20 @@ def run_single(args):
     dev = torch.device("cuda", 0)
     _b.build()
     n = args.n
+    if args.only in ("guard_f64_illcond", "proj_f32c_sym6"):
+        if args.only == "guard_f64_illcond":
+            A = W.illconditioned(n, dev, seed=1104, log10_kappa_max=4.0).A
+            lam = torch.empty(n, 3, dtype=torch.float64, device=dev)
+            fn = lambda: eig3.eigvals(A, precision="f64g", out=lam)
+        else:
+            A = W.workload3(n=n, device=dev).A
+            P = torch.empty(n, 3, 3, 3, dtype=torch.float32, device=dev)
+            fn = lambda: eig3.eigprojectors(A, precision="f32c", out=P)
+        for _ in range(args.warmup):
+            fn()
+        ms = timed(fn, args.steps, torch.cuda.current_stream(dev))
+        print(json.dumps({"kernel": args.only, "n": n, "ms": ms, "G_matrices_per_s": n / ms / 1e6}))
+        return 0
     if args.only.startswith("mc_"):
         prec = "f32c" if "f32c" in args.only else "f64"
         A = W.stress_field(n, dev, seed=1006).A

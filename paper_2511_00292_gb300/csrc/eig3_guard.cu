@@ -81,11 +81,15 @@ __device__ __forceinline__ void eig2x2(double a, double b, double c, double d, d
   l2 = d - bc / t;
 }
 
-// Plane rotation (c, s) with c x + s y = hypot(x, y) and -s x + c y = 0.
+// Plane rotation (c, s) with c x + s y = sqrt(x^2 + y^2) and -s x + c y = 0.
+// The QR iteration runs on the matrix scaled to entries below 2 in magnitude,
+// so x^2 + y^2 cannot overflow; below the normal range it is treated as 0.
 __device__ __forceinline__ void rotation(double x, double y, double &c, double &s) {
-  const double r = hypot(x, y);
-  c = r > 0.0 ? x / r : 1.0;
-  s = r > 0.0 ? y / r : 0.0;
+  const double r2 = fma(x, x, y * y);
+  const bool ok = r2 >= 2.2250738585072014e-308;
+  const double t = rsqrt(ok ? r2 : 1.0);
+  c = ok ? x * t : 1.0;
+  s = ok ? y * t : 0.0;
 }
 
 // (p, q) <- (c p + s q, -s p + c q): the rotation applied to two entries of a
@@ -108,9 +112,15 @@ __device__ __forceinline__ void sort3(double &x, double &y, double &z) {
 // non-finite input, or no convergence, gives NaNs.  Not inlined: only the
 // switched matrices call it, and the common path keeps its compact code.
 __device__ __noinline__ Eig eigvals_qr(const double (&a)[9]) {
-  double h00 = a[0], h01 = a[1], h02 = a[2];
-  double h10 = a[3], h11 = a[4], h12 = a[5];
-  double h20 = a[6], h21 = a[7], h22 = a[8];
+  // exact power-of-two scaling: the largest magnitude into [1, 2)
+  int hm = hi_abs(a[0]);
+#pragma unroll
+  for (int j = 1; j < 9; ++j) hm = max(hm, hi_abs(a[j]));
+  const int e = min(max(hm >> 20, 1), 2045) - 1023;
+  const double sc = pow2d(-e);
+  double h00 = a[0] * sc, h01 = a[1] * sc, h02 = a[2] * sc;
+  double h10 = a[3] * sc, h11 = a[4] * sc, h12 = a[5] * sc;
+  double h20 = a[6] * sc, h21 = a[7] * sc, h22 = a[8] * sc;
   if (h20 != 0.0) {  // Hessenberg form: G H G^T with G acting on rows/columns 1, 2
     double c, s;
     rotation(h10, h20, c, s);
@@ -163,18 +173,20 @@ __device__ __noinline__ Eig eigvals_qr(const double (&a)[9]) {
     h21 = r21;      h22 = b22 + sg;
   }
   sort3(l1, l2, l3);
-  Eig e;
-  e.l1 = l1;
-  e.l2 = l2;
-  e.l3 = l3;
+  const double us = pow2d(e);  // back from the scaling
+  Eig o;
+  o.l1 = l1 * us;
+  o.l2 = l2 * us;
+  o.l3 = l3 * us;
+  // adjoint inputs from the gaps (scale-free sigmas; r scaled back)
   const double g12 = l2 - l1, g23 = l3 - l2;
   const double r = sqrt(fma(g12, g12, fma(g12, g23, g23 * g23)));
-  e.r = r;
-  e.sigma1 = r > 0.0 ? kHalfSqrt3 * g12 / r : 0.0;
-  e.sigma2 = r > 0.0 ? kHalfSqrt3 * g23 / r : 0.0;
-  e.j2_clamped = false;
-  e.d_clamped = false;
-  return e;
+  o.r = r * us;
+  o.sigma1 = r > 0.0 ? kHalfSqrt3 * g12 / r : 0.0;
+  o.sigma2 = r > 0.0 ? kHalfSqrt3 * g23 / r : 0.0;
+  o.j2_clamped = false;
+  o.d_clamped = false;
+  return o;
 }
 
 // The binary64 path's eigenvalues, or the QR algorithm's for a strongly
