@@ -509,7 +509,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
     ogG = torch.empty_like(hG).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
     d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
-    pipe = HostPipeline(dev, chunk=1 << 22, depth=3)
+    pipe = HostPipeline(dev, chunk=1 << 21, depth=3)
 
     graph = pipe.capture([(hS, hwS, olS, ogS, None, "f32c"), (hG, hwG, olG, ogG, None, "f64")])
 
@@ -525,7 +525,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
         bool(torch.equal(olS[:1024], eig3.eigvals(S.A[:1024], precision="f32c").cpu()))
     del hS, hG, hwS, hwG, olS, olG, ogS, ogG, pipe
     return {"value": (S.n + G.n) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "mode": "pinned host buffers, chunks of 2^22 streamed through 3 device slots "
+            "mode": "pinned host buffers, chunks of 2^21 streamed through 3 device slots "
                     "(H2D / kernels / D2H on 3 streams), captured once as a CUDA graph",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
             "results_match_device": ok}
