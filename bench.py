@@ -520,6 +520,29 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
     torch.cuda.synchronize(dev)
     k = max(1, min(steps, 3))
     ms = timed(step, k, stream)
+    # the copy ceiling on this machine: the same pinned buffers, 1 GiB each way
+    # at once (host-to-device on one stream, device-to-host on another)
+    nb = 1 << 30
+    src_h = hG.view(-1).view(torch.uint8)[:nb]
+    dst_h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty(2, nb, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def both():
+        s1.wait_stream(stream)
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s1):
+            dbuf[0].copy_(src_h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            dst_h.copy_(dbuf[1], non_blocking=True)
+        stream.wait_stream(s1)
+        stream.wait_stream(s2)
+
+    both()
+    t_both = timed(both, 3, stream) * 1e-3
+    each_gbs = nb / t_both / 1e9
+    floor_ms = max(h2d, d2h) / (each_gbs * 1e9) * 1e3
+    del dbuf, dst_h
     # the results are the device results: spot-check one chunk of each half
     ok = bool(torch.equal(olG[:1024], eig3.eigvals(G.A[:1024]).cpu())) and \
         bool(torch.equal(olS[:1024], eig3.eigvals(S.A[:1024], precision="f32c").cpu()))
@@ -528,7 +551,9 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
             "mode": "pinned host buffers, chunks of 2^21 streamed through 3 device slots "
                     "(H2D / kernels / D2H on 3 streams), captured once as a CUDA graph",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
-            "results_match_device": ok}
+            "results_match_device": ok,
+            "copy_roofline": {"both_directions_gbs_each": each_gbs, "floor_ms": floor_ms,
+                              "frac": floor_ms / ms}}
 
 
 def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
