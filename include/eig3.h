@@ -136,6 +136,11 @@ eig3_status eig3_invariants(const void *A, int layout, int dtype, int precision,
  *          values the adjoint needs, (r, sigma_1, sigma_2, I1) with
  *          r = sqrt(3 J2+), sigma_1 = sin(phi/3), sigma_2 = sin((pi-phi)/3);
  *          pass it back to eig3_eigvals_backward to skip the recomputation.
+ *          For a matrix that EIG3_PREC_F64_GUARDED switched to the QR
+ *          algorithm the same quantities follow from its eigenvalue gaps:
+ *          r^2 = g12^2 + g12 g23 + g23^2, sigma_1 = (sqrt3/2) g12 / r,
+ *          sigma_2 = (sqrt3/2) g23 / r (g12 = lambda_2 - lambda_1,
+ *          g23 = lambda_3 - lambda_2), and I1 is the trace.
  *   stats  device eig3_stats or NULL (see eig3_stats_reset).
  */
 eig3_status eig3_eigvals(const void *A, int layout, int dtype, int precision, int64_t n,
