@@ -1,9 +1,11 @@
 // eig3_f32c.cu -- compensated binary32 kernels (storage and arithmetic in
 // binary32, see eig3_f32c.cuh): invariants, eigenvalues (+ adjoint inputs,
-// + statistics) and the adjoint, for both layouts.  One thread per matrix;
-// blocks walk the batch in tiles of 256 rows whose inputs are copied into
-// shared memory asynchronously, one tile ahead (eig3_tile.cuh); the 16-byte
-// adjoint-input rows move as one float4 each; outputs are stored directly.
+// + statistics), the adjoint and the eigenprojectors, for both layouts.  One
+// thread per matrix; blocks walk the batch in tiles of 256 rows whose inputs
+// are copied into shared memory asynchronously, one tile ahead (for_each_row /
+// for_each_tile, eig3_tile.cuh); the 16-byte adjoint-input rows move as one
+// float4 each; outputs are stored directly, the projectors through shared
+// memory.
 #include <cstdint>
 
 #include "eig3_f32c.cuh"
@@ -69,47 +71,30 @@ __global__ void __launch_bounds__(kThreads)
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
   const bool vaux = AUX && aligned16c(aux);
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles)
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kTile;
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) {
-      float a[N];
+  for_each_row<N, float>(A, n, sA, [&](int64_t i, const float *row) {
+    float a[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
-      const InvC v = invariants_c<LAYOUT, N>(a);
-      const EigC e = eigvals_c(v);
-      const int64_t i = r0 + threadIdx.x;
-      lam[3 * i + 0] = e.l1;
-      lam[3 * i + 1] = e.l2;
-      lam[3 * i + 2] = e.l3;
-      if constexpr (AUX) {
-        if (vaux) {
-          *reinterpret_cast<float4 *>(aux + 4 * i) = make_float4(e.r, e.sigma1, e.sigma2, e.I1);
-        } else {
-          aux[4 * i] = e.r;
-          aux[4 * i + 1] = e.sigma1;
-          aux[4 * i + 2] = e.sigma2;
-          aux[4 * i + 3] = e.I1;
-        }
-      }
-      if constexpr (STATS) {
-        stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0f, fminf(e.sigma1, e.sigma2), e.l1,
-                 e.l2, e.l3);
+    for (int j = 0; j < N; ++j) a[j] = row[j];
+    const InvC v = invariants_c<LAYOUT, N>(a);
+    const EigC e = eigvals_c(v);
+    lam[3 * i + 0] = e.l1;
+    lam[3 * i + 1] = e.l2;
+    lam[3 * i + 2] = e.l3;
+    if constexpr (AUX) {
+      if (vaux) {
+        *reinterpret_cast<float4 *>(aux + 4 * i) = make_float4(e.r, e.sigma1, e.sigma2, e.I1);
+      } else {
+        aux[4 * i] = e.r;
+        aux[4 * i + 1] = e.sigma1;
+        aux[4 * i + 2] = e.sigma2;
+        aux[4 * i + 3] = e.I1;
       }
     }
-    buf ^= 1;
-  }
+    if constexpr (STATS) {
+      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0f, fminf(e.sigma1, e.sigma2), e.l1,
+               e.l2, e.l3);
+    }
+  });
   if constexpr (STATS) stat_flush(acc, stats);
 }
 
@@ -121,64 +106,45 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ __align__(16) float sA[2][kTile * N];
   __shared__ __align__(16) float sG[2][kTile * 3];
   const bool vaux = AUX && aligned16c(aux);
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles) {
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-    tile_issue(g, (int64_t)blockIdx.x * kTile * 3, rows_of(blockIdx.x) * 3, sG[0]);
-  }
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kTile;
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) {
-      tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-      tile_issue(g, tn * kTile * 3, rows_of(tn) * 3, sG[buf ^ 1]);
-    }
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) {
-      float a[N];
+  for_each_tile<N, 3, float, float>(A, g, n, sA, sG, [&](int64_t r0, int rows, const float *tA,
+                                                         const float *tG) {
+    if ((int)threadIdx.x >= rows) return;
+    float a[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
-      const float g1 = sG[buf][threadIdx.x * 3 + 0];
-      const float g2 = sG[buf][threadIdx.x * 3 + 1];
-      const float g3 = sG[buf][threadIdx.x * 3 + 2];
-      const int64_t i = r0 + threadIdx.x;
-      float r, s1, s2;
-      if constexpr (AUX) {
-        if (vaux) {
-          const float4 x = __ldg(reinterpret_cast<const float4 *>(aux + 4 * i));
-          r = x.x;
-          s1 = x.y;
-          s2 = x.z;
-        } else {
-          r = __ldg(aux + 4 * i);
-          s1 = __ldg(aux + 4 * i + 1);
-          s2 = __ldg(aux + 4 * i + 2);
-        }
+    for (int j = 0; j < N; ++j) a[j] = tA[threadIdx.x * N + j];
+    const float g1 = tG[threadIdx.x * 3 + 0];
+    const float g2 = tG[threadIdx.x * 3 + 1];
+    const float g3 = tG[threadIdx.x * 3 + 2];
+    const int64_t i = r0 + threadIdx.x;
+    float r, s1, s2;
+    if constexpr (AUX) {
+      if (vaux) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(aux + 4 * i));
+        r = x.x;
+        s1 = x.y;
+        s2 = x.z;
       } else {
-        const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
-        r = e.r;
-        s1 = e.sigma1;
-        s2 = e.sigma2;
+        r = __ldg(aux + 4 * i);
+        s1 = __ldg(aux + 4 * i + 1);
+        s2 = __ldg(aux + 4 * i + 2);
       }
-      const AdjC s = adjoint_c(r, s1, s2, g1, g2, g3);
-      float G[N];
-      if constexpr (LAYOUT == EIG3_GENERAL9) {
-        grad_general_c(a, s, G);
-      } else {
-        grad_sym_c(a, s, G);
-      }
-      float *q = gA + N * i;
-#pragma unroll
-      for (int j = 0; j < N; ++j) q[j] = G[j];
+    } else {
+      const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+      r = e.r;
+      s1 = e.sigma1;
+      s2 = e.sigma2;
     }
-    buf ^= 1;
-  }
+    const AdjC s = adjoint_c(r, s1, s2, g1, g2, g3);
+    float G[N];
+    if constexpr (LAYOUT == EIG3_GENERAL9) {
+      grad_general_c(a, s, G);
+    } else {
+      grad_sym_c(a, s, G);
+    }
+    float *q = gA + N * i;
+#pragma unroll
+    for (int j = 0; j < N; ++j) q[j] = G[j];
+  });
 }
 
 template <int LAYOUT, bool LAM>
@@ -191,41 +157,29 @@ __global__ void __launch_bounds__(kThreads)
   // stride between lanes when stored directly)
   __shared__ __align__(16) float sP[kTile * 27];
   __shared__ __align__(16) float sL[LAM ? kTile * 3 : 4];
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles)
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kTile;
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();  // also: every thread is done storing the previous tile's outputs
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) {
-      float a[N];
+  for_each_tile<N, 0, float, float>(
+      A, (const float *)nullptr, n, sA, (float(*)[kTile])nullptr,
+      [&](int64_t r0, int rows, const float *tA, const float *) {
+        if ((int)threadIdx.x < rows) {
+          float a[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) a[j] = sA[buf][threadIdx.x * N + j];
-      const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
-      if constexpr (LAM) {
-        sL[3 * threadIdx.x + 0] = e.l1;
-        sL[3 * threadIdx.x + 1] = e.l2;
-        sL[3 * threadIdx.x + 2] = e.l3;
-      }
-      float E[27];
-      projectors_c<N>(a, adjoint_units_c(e.r, e.sigma1, e.sigma2), E);
-      float *q = sP + 27 * threadIdx.x;
+          for (int j = 0; j < N; ++j) a[j] = tA[threadIdx.x * N + j];
+          const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+          if constexpr (LAM) {
+            sL[3 * threadIdx.x + 0] = e.l1;
+            sL[3 * threadIdx.x + 1] = e.l2;
+            sL[3 * threadIdx.x + 2] = e.l3;
+          }
+          float E[27];
+          projectors_c<N>(a, adjoint_units_c(e.r, e.sigma1, e.sigma2), E);
+          float *q = sP + 27 * threadIdx.x;
 #pragma unroll
-      for (int j = 0; j < 27; ++j) q[j] = E[j];
-    }
-    __syncthreads();
-    tile_store(sP, rows * 27, P, r0 * 27);
-    if constexpr (LAM) tile_store(sL, rows * 3, lam, r0 * 3);
-    buf ^= 1;
-  }
+          for (int j = 0; j < 27; ++j) q[j] = E[j];
+        }
+        __syncthreads();  // the tile's outputs are staged; the next barrier protects them
+        tile_store(sP, rows * 27, P, r0 * 27);
+        if constexpr (LAM) tile_store(sL, rows * 3, lam, r0 * 3);
+      });
 }
 
 template <int LAYOUT>

@@ -5,9 +5,9 @@
 // One thread per matrix.  Blocks of 256 threads walk the batch in tiles of 256
 // rows (grid-stride over tiles, grid sized to fill every SM).  The input rows
 // of the next tile are copied into shared memory with asynchronous 16-byte
-// copies while the current tile is computed (eig3_tile.cuh); the adjoint
-// inputs (16- or 32-byte rows) move with direct vector accesses and the
-// outputs are stored directly.  The binary64 path is bound by the FP64 pipe
+// copies while the current tile is computed (for_each_row / for_each_tile,
+// eig3_tile.cuh); the adjoint inputs (16- or 32-byte rows) move with direct
+// vector accesses and the outputs are stored directly.  The binary64 path is bound by the FP64 pipe
 // (two DFMA per SM per clock on GB300, far below what HBM could feed).
 #include <cstdint>
 
@@ -133,41 +133,24 @@ __global__ void __launch_bounds__(kThreads)
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
   const bool vaux = AUX && aligned16(aux);
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles)
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kTile;
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();  // tile t is in sA[buf]; every thread is done with sA[buf ^ 1]
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) {
-      double a[N];
+  for_each_row<N, T>(A, n, sA, [&](int64_t i, const T *row) {
+    double a[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) a[j] = (double)sA[buf][threadIdx.x * N + j];
-      const Inv v = invariants_of<LAYOUT, N>(a);
-      const Eig e = eigvals_from_inv(v);
-      const int64_t i = r0 + threadIdx.x;
-      lam[3 * i + 0] = (T)e.l1;
-      lam[3 * i + 1] = (T)e.l2;
-      lam[3 * i + 2] = (T)e.l3;
-      if constexpr (AUX) {
-        const double x[4] = {e.r, e.sigma1, e.sigma2, v.I1};
-        store_aux<T>(aux, i, vaux, x);
-      }
-      if constexpr (STATS) {
-        stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
-                 seed_float(min_nonneg(e.sigma1, e.sigma2)), (T)e.l1, (T)e.l2, (T)e.l3);
-      }
+    for (int j = 0; j < N; ++j) a[j] = (double)row[j];
+    const Inv v = invariants_of<LAYOUT, N>(a);
+    const Eig e = eigvals_from_inv(v);
+    lam[3 * i + 0] = (T)e.l1;
+    lam[3 * i + 1] = (T)e.l2;
+    lam[3 * i + 2] = (T)e.l3;
+    if constexpr (AUX) {
+      const double x[4] = {e.r, e.sigma1, e.sigma2, v.I1};
+      store_aux<T>(aux, i, vaux, x);
     }
-    buf ^= 1;
-  }
+    if constexpr (STATS) {
+      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
+               seed_float(min_nonneg(e.sigma1, e.sigma2)), (T)e.l1, (T)e.l2, (T)e.l3);
+    }
+  });
   if constexpr (STATS) stat_flush(acc, stats);
 }
 
@@ -179,55 +162,36 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ __align__(16) T sA[2][kTile * N];
   __shared__ __align__(16) T sG[2][kTile * 3];
   const bool vaux = AUX && aligned16(aux);
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles) {
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-    tile_issue(g, (int64_t)blockIdx.x * kTile * 3, rows_of(blockIdx.x) * 3, sG[0]);
-  }
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kTile;
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) {
-      tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-      tile_issue(g, tn * kTile * 3, rows_of(tn) * 3, sG[buf ^ 1]);
-    }
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) {
-      double a[N];
+  for_each_tile<N, 3, T, T>(A, g, n, sA, sG, [&](int64_t r0, int rows, const T *tA,
+                                                 const T *tG) {
+    if ((int)threadIdx.x >= rows) return;
+    double a[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) a[j] = (double)sA[buf][threadIdx.x * N + j];
-      const double g1 = (double)sG[buf][threadIdx.x * 3 + 0];
-      const double g2 = (double)sG[buf][threadIdx.x * 3 + 1];
-      const double g3 = (double)sG[buf][threadIdx.x * 3 + 2];
-      const int64_t i = r0 + threadIdx.x;
-      double r, s1, s2;
-      if constexpr (AUX) {
-        load_aux<T>(aux, i, vaux, r, s1, s2);
-      } else {
-        const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
-        r = e.r;
-        s1 = e.sigma1;
-        s2 = e.sigma2;
-      }
-      const Adj s = adjoint_scalars(r, s1, s2, g1, g2, g3);
-      double G[N];
-      if constexpr (LAYOUT == EIG3_GENERAL9) {
-        grad_general(a, s, G);
-      } else {
-        grad_sym(a, s, G);
-      }
-      T *q = gA + N * i;
-#pragma unroll
-      for (int j = 0; j < N; ++j) q[j] = (T)G[j];
+    for (int j = 0; j < N; ++j) a[j] = (double)tA[threadIdx.x * N + j];
+    const double g1 = (double)tG[threadIdx.x * 3 + 0];
+    const double g2 = (double)tG[threadIdx.x * 3 + 1];
+    const double g3 = (double)tG[threadIdx.x * 3 + 2];
+    const int64_t i = r0 + threadIdx.x;
+    double r, s1, s2;
+    if constexpr (AUX) {
+      load_aux<T>(aux, i, vaux, r, s1, s2);
+    } else {
+      const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
+      r = e.r;
+      s1 = e.sigma1;
+      s2 = e.sigma2;
     }
-    buf ^= 1;
-  }
+    const Adj s = adjoint_scalars(r, s1, s2, g1, g2, g3);
+    double G[N];
+    if constexpr (LAYOUT == EIG3_GENERAL9) {
+      grad_general(a, s, G);
+    } else {
+      grad_sym(a, s, G);
+    }
+    T *q = gA + N * i;
+#pragma unroll
+    for (int j = 0; j < N; ++j) q[j] = (T)G[j];
+  });
 }
 
 template <int LAYOUT, typename T, bool LAM>
@@ -235,39 +199,22 @@ __global__ void __launch_bounds__(kThreads)
     k_projectors(const T *__restrict__ A, int64_t n, T *__restrict__ lam, T *__restrict__ P) {
   constexpr int N = Width<LAYOUT>::N;
   __shared__ __align__(16) T sA[2][kTile * N];
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles)
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kTile;
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) {
-      double a[N];
+  for_each_row<N, T>(A, n, sA, [&](int64_t i, const T *row) {
+    double a[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) a[j] = (double)sA[buf][threadIdx.x * N + j];
-      const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
-      const int64_t i = r0 + threadIdx.x;
-      if constexpr (LAM) {
-        lam[3 * i + 0] = (T)e.l1;
-        lam[3 * i + 1] = (T)e.l2;
-        lam[3 * i + 2] = (T)e.l3;
-      }
-      double E[27];
-      projectors<N>(a, adjoint_units(e.r, e.sigma1, e.sigma2), E);
-      T *q = P + 27 * i;
-#pragma unroll
-      for (int j = 0; j < 27; ++j) q[j] = (T)E[j];
+    for (int j = 0; j < N; ++j) a[j] = (double)row[j];
+    const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
+    if constexpr (LAM) {
+      lam[3 * i + 0] = (T)e.l1;
+      lam[3 * i + 1] = (T)e.l2;
+      lam[3 * i + 2] = (T)e.l3;
     }
-    buf ^= 1;
-  }
+    double E[27];
+    projectors<N>(a, adjoint_units(e.r, e.sigma1, e.sigma2), E);
+    T *q = P + 27 * i;
+#pragma unroll
+    for (int j = 0; j < 27; ++j) q[j] = (T)E[j];
+  });
 }
 
 template <int LAYOUT, typename T>

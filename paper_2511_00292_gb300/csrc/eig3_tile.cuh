@@ -78,29 +78,53 @@ __device__ __forceinline__ void tile_store(const E *__restrict__ s, int count,
   for (int i = head + threadIdx.x; i < count; i += blockDim.x) dst[i] = s[i];
 }
 
-// The loop above as one call: walks the batch of n rows of N elements in
-// tiles (grid-stride over tiles, the next tile staged while the current one
-// is computed) and calls body(row_index, row) for every row, with row
-// pointing into shared memory.  sA holds two tiles.
+// The loop above as one call.  Walks the batch of n rows in tiles of kTile
+// rows (grid-stride over tiles): the rows of the next tile -- N elements each
+// from A and, when M > 0, M elements each from B -- are copied into shared
+// memory (sA, sB: two tiles each) while the current one is computed, and
+// fn(r0, rows, tileA, tileB) is called once per tile by every thread of the
+// block (r0 the tile's first row, rows its row count, tileA/tileB its rows in
+// shared memory).  fn may end with a block barrier of its own (e.g. before a
+// tile_store of staged outputs); the barrier at the top of the next iteration
+// keeps the buffers apart.
+template <int N, int M, typename T, typename U, typename Fn>
+__device__ __forceinline__ void for_each_tile(const T *__restrict__ A, const U *__restrict__ B,
+                                              int64_t n, T (*sA)[kTile * N],
+                                              U (*sB)[kTile * (M > 0 ? M : 1)], Fn fn) {
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
+  auto issue = [&](int64_t t, int b) {
+    tile_issue(A, t * kTile * N, rows_of(t) * N, sA[b]);
+    if constexpr (M > 0) tile_issue(B, t * kTile * M, rows_of(t) * M, sB[b]);
+  };
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  cp_async_commit();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();  // tile t has landed; every thread is done with the other buffers
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) issue(tn, buf ^ 1);
+    cp_async_commit();
+    if constexpr (M > 0) {
+      fn(t * kTile, rows_of(t), sA[buf], sB[buf]);
+    } else {
+      fn(t * kTile, rows_of(t), sA[buf], (const U *)nullptr);
+    }
+    buf ^= 1;
+  }
+}
+
+// for_each_tile for one input array, calling body(row_index, row) for every
+// row of the batch (row points into shared memory).
 template <int N, typename T, typename Body>
 __device__ __forceinline__ void for_each_row(const T *__restrict__ A, int64_t n, T (*sA)[kTile * N],
                                              Body body) {
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kTile, n - t * kTile); };
-  int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles)
-    tile_issue(A, (int64_t)blockIdx.x * kTile * N, rows_of(blockIdx.x) * N, sA[0]);
-  cp_async_commit();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int rows = rows_of(t);
-    cp_async_wait_all();
-    __syncthreads();  // tile t is in sA[buf]; every thread is done with sA[buf ^ 1]
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) tile_issue(A, tn * kTile * N, rows_of(tn) * N, sA[buf ^ 1]);
-    cp_async_commit();
-    if ((int)threadIdx.x < rows) body(t * kTile + threadIdx.x, &sA[buf][threadIdx.x * N]);
-    buf ^= 1;
-  }
+  for_each_tile<N, 0, T, T>(A, (const T *)nullptr, n, sA, (T(*)[kTile])nullptr,
+                            [&](int64_t r0, int rows, const T *tile, const T *) {
+                              if ((int)threadIdx.x < rows)
+                                body(r0 + threadIdx.x, tile + threadIdx.x * N);
+                            });
 }
 
 }  // namespace eig3
