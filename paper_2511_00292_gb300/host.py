@@ -29,14 +29,35 @@ class HostPipeline:
         self.s_out = torch.cuda.Stream(self.dev)
         self._slots = {}
 
+    # The device slots of a slot set are one fresh allocation, cut at 2 MiB
+    # boundaries.  Cached allocator blocks that earlier kernels had written
+    # took host-to-device copies at 20-100 GB/s instead of 200 GB/s, so the
+    # allocator's cache is released first and the slots come from new device
+    # memory (a one-time cost per slot set).
+    _ALIGN = 1 << 21
+
     def _get_slots(self, key, width, dtype):
         if key not in self._slots:
-            c, d = self.chunk, self.depth
-            mk = lambda w: [torch.empty((c, w), dtype=dtype, device=self.dev) for _ in range(d)]
-            self._slots[key] = dict(A=mk(width), w=mk(3), lam=mk(3), aux=mk(4), g=mk(width),
-                                    free=[torch.cuda.Event() for _ in range(d)],
-                                    loaded=[torch.cuda.Event() for _ in range(d)],
-                                    done=[torch.cuda.Event() for _ in range(d)])
+            c, d, al = self.chunk, self.depth, self._ALIGN
+            esize = torch.empty((), dtype=dtype).element_size()
+            widths = {"A": width, "w": 3, "lam": 3, "aux": 4, "g": width}
+            span = lambda w: (c * w * esize + al - 1) // al * al
+            total = d * sum(span(w) for w in widths.values())
+            torch.cuda.synchronize(self.dev)
+            torch.cuda.empty_cache()
+            raw = torch.empty(total + al, dtype=torch.uint8, device=self.dev)
+            off = (-raw.data_ptr()) % al
+            slots = {}
+            for name, w in widths.items():
+                views = []
+                for _ in range(d):
+                    views.append(raw[off:off + c * w * esize].view(dtype).view(c, w))
+                    off += span(w)
+                slots[name] = views
+            slots.update(raw=raw, free=[torch.cuda.Event() for _ in range(d)],
+                         loaded=[torch.cuda.Event() for _ in range(d)],
+                         done=[torch.cuda.Event() for _ in range(d)])
+            self._slots[key] = slots
         return self._slots[key]
 
     def forward_backward(self, A: torch.Tensor, w: torch.Tensor, lam_out: torch.Tensor,
