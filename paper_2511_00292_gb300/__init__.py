@@ -11,8 +11,14 @@ Layouts: ``"general9"`` (n, 9) row-major, or (n, 3, 3); ``"sym6"`` (n, 6) in
 the order (A00, A11, A22, A12, A02, A01).
 Precisions: ``"f64"`` (binary64 arithmetic; storage float64 or float32),
 ``"f32c"`` (compensated binary32 arithmetic; storage float32) and ``"f64g"``
-(binary64 with the guard for ill-conditioned eigenbases: strongly non-normal
-matrices get compensated binary64 invariants).
+(binary64 with the guard for ill-conditioned eigenbases: a strongly non-normal
+matrix gets its eigenvalues from the shifted QR algorithm instead of the
+closed form; eigenvalues and adjoint only).
+
+Entry points: :func:`eigvals`, :func:`eigvals_backward`, :func:`eigvals_ad`
+(autograd), :func:`invariants`, :func:`eigprojectors`, :func:`mohr_coulomb`,
+:func:`eigvals_variant` (the paper's comparison variants), :class:`Stats`;
+host-resident batches stream through :class:`host.HostPipeline`.
 """
 from __future__ import annotations
 
@@ -24,10 +30,9 @@ from . import _lib
 from ._lib import (F32, F64, GENERAL9, PREC_F32_COMP, PREC_F64, SYM6, Eig3Error, Eig3Stats,
                    check, load)
 
-__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors", "mohr_coulomb",
-           "eigvals_variant",
-           "Stats",
-           "Eig3Error", "layout_of", "GENERAL9", "SYM6"]
+__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors",
+           "mohr_coulomb", "eigvals_variant", "Stats", "Eig3Error", "layout_of", "GENERAL9",
+           "SYM6"]
 
 _LAYOUTS = {"general9": GENERAL9, "sym6": SYM6, GENERAL9: GENERAL9, SYM6: SYM6}
 _PRECS = {"f64": PREC_F64, "f32c": PREC_F32_COMP, "f64g": _lib.PREC_F64_GUARDED,
@@ -91,6 +96,17 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _out(t, numel: int, dtype, name: str):
+    """A caller-supplied output: the kernels write numel elements of dtype
+    through its pointer, so it must hold exactly that, contiguously, where the
+    GPU can write it (device or pinned host memory)."""
+    if t.dtype != dtype or t.numel() != numel or not t.is_contiguous() or not (
+            t.is_cuda or t.is_pinned()):
+        raise ValueError(f"{name} must be a contiguous CUDA or pinned tensor of {numel} "
+                         f"{dtype} elements (got {tuple(t.shape)} {t.dtype})")
+    return t
+
+
 class Stats:
     """Device-resident eig3_stats accumulated by :func:`eigvals` (see eig3.h)."""
 
@@ -137,10 +153,13 @@ def eigvals(A: torch.Tensor, layout=None, precision="f64", return_aux=False, sta
     X = _rows(A, lay)
     n = X.shape[0]
     dev = _device(X, device)
-    lam = out if out is not None else _alloc((n, 3), X.dtype, X, dev)
+    lam = _out(out, 3 * n, X.dtype, "out") if out is not None else _alloc((n, 3), X.dtype, X, dev)
     aux = None
     if return_aux:
-        aux = aux_out if aux_out is not None else torch.empty((n, 4), dtype=X.dtype, device=dev)
+        aux = (_out(aux_out, 4 * n, X.dtype, "aux_out") if aux_out is not None
+               else torch.empty((n, 4), dtype=X.dtype, device=dev))
+    if stats is not None and not (stats.buf.is_cuda and stats.buf.numel() == 6):
+        raise ValueError("stats must be a Stats object")
     sp = _ptr(stats.buf) if stats is not None else None
     with torch.cuda.device(dev):
         st = load().eig3_eigvals(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n, _ptr(lam),
@@ -161,7 +180,8 @@ def eigvals_backward(A: torch.Tensor, grad_lam: torch.Tensor, aux=None, layout=N
     if aux is not None and (aux.dtype != X.dtype or aux.numel() != 4 * X.shape[0]):
         raise ValueError("aux must be the (n, 4) tensor returned by eigvals(return_aux=True)")
     dev = _device(X, device)
-    gA = out if out is not None else _alloc(tuple(X.shape), X.dtype, X, dev)
+    gA = (_out(out, X.numel(), X.dtype, "out") if out is not None
+          else _alloc(tuple(X.shape), X.dtype, X, dev))
     with torch.cuda.device(dev):
         st = load().eig3_eigvals_backward(_ptr(X), lay, _dtype_code(X), _PRECS[precision],
                                           X.shape[0], _ptr(g), _ptr(aux), _ptr(gA),
@@ -178,10 +198,12 @@ def eigprojectors(A: torch.Tensor, layout=None, precision="f64", return_eigvals=
     X = _rows(A, lay)
     n = X.shape[0]
     dev = _device(X, device)
-    P = out if out is not None else _alloc((n, 3, 3, 3), X.dtype, X, dev)
+    P = _out(out, 27 * n, X.dtype, "out") if out is not None else _alloc((n, 3, 3, 3), X.dtype,
+                                                                         X, dev)
     lam = None
     if return_eigvals:
-        lam = lam_out if lam_out is not None else _alloc((n, 3), X.dtype, X, dev)
+        lam = (_out(lam_out, 3 * n, X.dtype, "lam_out") if lam_out is not None
+               else _alloc((n, 3), X.dtype, X, dev))
     with torch.cuda.device(dev):
         st = load().eig3_eigprojectors(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n,
                                        _ptr(lam), _ptr(P), _stream(dev))
@@ -197,10 +219,11 @@ def mohr_coulomb(sigma: torch.Tensor, s_yc: float = 100.0, m: float = 10.0, layo
     X = _rows(sigma, lay)
     n = X.shape[0]
     dev = _device(X, device)
-    f = out if out is not None else _alloc((n,), X.dtype, X, dev)
+    f = _out(out, n, X.dtype, "out") if out is not None else _alloc((n,), X.dtype, X, dev)
     g = None
     if grad:
-        g = grad_out if grad_out is not None else _alloc(tuple(X.shape), X.dtype, X, dev)
+        g = (_out(grad_out, X.numel(), X.dtype, "grad_out") if grad_out is not None
+             else _alloc(tuple(X.shape), X.dtype, X, dev))
     with torch.cuda.device(dev):
         st = load().eig3_mohr_coulomb(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n,
                                       float(s_yc), float(m), _ptr(f), _ptr(g), _stream(dev))
@@ -223,10 +246,12 @@ def eigvals_variant(A: torch.Tensor, variant: str, layout=None, invariants=True,
     dev = _device(X, device)
     inv = None
     if invariants:
-        inv = inv_out if inv_out is not None else _alloc((n, 4), torch.float64, X, dev)
+        inv = (_out(inv_out, 4 * n, torch.float64, "inv_out") if inv_out is not None
+               else _alloc((n, 4), torch.float64, X, dev))
     lam = None
     if eigvals:
-        lam = lam_out if lam_out is not None else _alloc((n, 3), X.dtype, X, dev)
+        lam = (_out(lam_out, 3 * n, X.dtype, "lam_out") if lam_out is not None
+               else _alloc((n, 3), X.dtype, X, dev))
     with torch.cuda.device(dev):
         st = load().eig3_eigvals_variant(_ptr(X), lay, _dtype_code(X), _VARIANTS[variant], n,
                                          _ptr(inv), _ptr(lam), _stream(dev))

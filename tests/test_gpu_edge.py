@@ -334,3 +334,38 @@ def test_host_pipeline_graph_replay(eig3):
         torch.cuda.synchronize()
         assert all(torch.equal(o, r) for o, r in zip(outs, ref))
 
+
+
+def test_supplied_outputs_are_checked_before_any_launch(eig3):
+    """The kernels write through raw pointers, so the binding refuses outputs of
+    the wrong size, dtype or memory kind instead of letting a kernel write past
+    them."""
+    A = W.workload2(n=1000, device="cpu", seed=2204).A.to(dev())
+    S = W.workload3(n=1000, device="cpu", seed=2205).A.to(dev())
+    small = torch.empty(999, 3, dtype=torch.float64, device=dev())
+    with pytest.raises(ValueError):
+        eig3.eigvals(A, out=small)
+    with pytest.raises(ValueError):
+        eig3.eigvals(A, out=torch.empty(1000, 3, dtype=torch.float32, device=dev()))
+    with pytest.raises(ValueError):
+        eig3.eigvals(A, out=torch.empty(1000, 3, dtype=torch.float64))          # pageable host
+    with pytest.raises(ValueError):
+        eig3.eigvals(A, return_aux=True, aux_out=torch.empty(1000, 3, dtype=torch.float64,
+                                                             device=dev()))
+    with pytest.raises(ValueError):
+        eig3.eigvals_backward(A, torch.zeros(1000, 3, dtype=torch.float64, device=dev()),
+                              out=torch.empty(1000, 6, dtype=torch.float64, device=dev()))
+    with pytest.raises(ValueError):
+        eig3.eigprojectors(A, out=torch.empty(1000, 26, dtype=torch.float64, device=dev()))
+    with pytest.raises(ValueError):
+        eig3.mohr_coulomb(S, grad=True, grad_out=torch.empty(1000, 9, dtype=torch.float32,
+                                                             device=dev()))
+    with pytest.raises(ValueError):
+        eig3.eigvals_variant(A, "naive", inv_out=torch.empty(1000, 4, dtype=torch.float32,
+                                                             device=dev()))
+    wide = torch.empty(1000, 6, dtype=torch.float64, device=dev())[:, :3]  # not contiguous
+    with pytest.raises(ValueError):
+        eig3.eigvals(A, out=wide)
+    # correct outputs are used as given
+    lam = torch.empty(1000, 3, dtype=torch.float64, device=dev())
+    assert eig3.eigvals(A, out=lam).data_ptr() == lam.data_ptr()
