@@ -72,10 +72,15 @@ class HostPipeline:
         """Several forward_backward jobs, (A, w, lam_out, grad_out, layout,
         precision) each, streamed back to back: the chunks of the next job enter
         the pipeline while the last ones of the previous job are still in it."""
-        for job in jobs:
-            for t in job[:4]:
-                if t.is_cuda or not t.is_pinned():
-                    raise ValueError("HostPipeline works on pinned host tensors")
+        for A, w, lam_out, grad_out, layout, _ in jobs:
+            for t in (A, w, lam_out, grad_out):
+                if t.is_cuda or not t.is_pinned() or not t.is_contiguous():
+                    raise ValueError("HostPipeline works on contiguous pinned host tensors")
+            n = A.numel() // (9 if layout_of(A, layout) == 0 else 6)
+            if any(t.dtype != A.dtype for t in (w, lam_out, grad_out)) or w.numel() != 3 * n \
+                    or lam_out.numel() != 3 * n or grad_out.numel() != A.numel():
+                raise ValueError("w and lam_out must hold (n, 3) and grad_out A's shape, all in "
+                                 "A's dtype")
         main = torch.cuda.current_stream(self.dev)
         for s in (self.s_in, self.s_run, self.s_out):
             s.wait_stream(main)
