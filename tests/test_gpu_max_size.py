@@ -1,0 +1,61 @@
+"""Batches beyond 2^31 matrices: row indices and element offsets past 32 bits.
+
+2^31 + 77 symmetric binary32 matrices (51.5 GB of input) through the
+compensated kernels and the binary64 kernels; rows sampled around 2^31 and at
+the ragged end are compared with the oracle, and every row with the result of
+the same matrix computed in a small batch (the rows repeat a small batch)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+SYM = 1
+
+
+@pytest.fixture(scope="module")
+def eig3():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_00292_gb300 as m
+    return m
+
+
+def test_more_than_2_31_rows(eig3):
+    dev = torch.device("cuda:0")
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 110e9:
+        pytest.skip("needs about 110 GB of free device memory")
+    base_n = 1 << 20
+    base = W.workload3(n=base_n, device=dev, seed=9301).A
+    tail = W.workload3(n=77, device=dev, seed=9302).A
+    n = (1 << 31) + 77
+    A = torch.empty(n, 6, dtype=torch.float32, device=dev)
+    A[: 1 << 31].view(1 << 11, base_n, 6).copy_(base.unsqueeze(0).expand(1 << 11, base_n, 6))
+    A[1 << 31:] = tail
+    ref_base = eig3.eigvals(base, precision="f32c")
+    ref_tail = eig3.eigvals(tail, precision="f32c")
+    lam = eig3.eigvals(A, precision="f32c")
+    torch.cuda.synchronize()
+    # every row equals the small-batch result of the same matrix
+    assert torch.equal(lam[: 1 << 31].view(1 << 11, base_n, 3),
+                       ref_base.unsqueeze(0).expand(1 << 11, base_n, 3))
+    assert torch.equal(lam[1 << 31:], ref_tail)
+    # and the rows around 2^31 and at the end agree with the oracle
+    idx = torch.cat([torch.arange((1 << 31) - 64, n, device=dev)])
+    X = U.to_np(A[idx])
+    err, tol, _ = U.check_eig_f32c(U.to_np(lam[idx]), X, 1.0, SYM)
+    assert np.all(err <= tol)
+    del lam
+    # binary64 arithmetic on the same binary32 storage
+    lam64 = eig3.eigvals(A, precision="f64")
+    base64 = eig3.eigvals(base, precision="f64")
+    torch.cuda.synchronize()
+    assert torch.equal(lam64[(1 << 31) - base_n: 1 << 31], base64)
+    assert torch.equal(lam64[1 << 31:], eig3.eigvals(tail, precision="f64"))
+    err, tol, bad = U.check_eig_f64(U.to_np(lam64[idx]), X, np.ones(len(X)), SYM,
+                                    f32_storage=True)
+    assert not bad.any()
