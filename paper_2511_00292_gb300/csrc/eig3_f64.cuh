@@ -106,7 +106,7 @@ __device__ __forceinline__ int dev_scale(double (&v)[N]) {
 //
 // Factored forms used below (each is the paper's r_i regrouped, no terms
 // dropped; the diagonal still enters only through d0, d1, d2):
-//   r1  = (M01 M12) M20 - (M02 M10) M21
+//   r1  = (M01 M12) M20 - (M02 M10) M21      (for A^T: -r1 of A)
 //   r2  = M01 X - M02 (M02 M21),              X = M01 M12 - M02 d2
 //   r3  = M01 (M21 d1 - M01 M20) + M21 (M02 M21)
 //   r4  = M12 (M02 d0 + M01 M12) - M02 (M02 M10)
@@ -128,19 +128,18 @@ struct DxShared {
 };
 
 struct Dx {
-  double r1, r2, r3, r4, r5, r6, r7, r8, r9, r10, r11, r12, r13;
+  double r2, r3, r4, r5, r6, r7, r8, r9, r10, r11, r12, r13;  // r1 is formed by the caller
 };
 
+// r2 .. r13 of dx(M); m0112 = M01 M12 and m0210 = M02 M10 come from the caller
+// (for M = A they are shared with J3 and r1).
 __device__ __forceinline__ Dx dx13(double M01, double M02, double M10, double M12, double M20,
-                                   double M21, const DxShared &s) {
+                                   double M21, double m0112, double m0210, const DxShared &s) {
   Dx r;
-  const double m0112 = M01 * M12;
-  const double m0210 = M02 * M10;
   const double m0221 = M02 * M21;
   const double m0120 = M01 * M20;
   const double X = fma(-M02, s.d2, m0112);
   const double Y = fma(M12, s.d1, -m0210);
-  r.r1 = fma(m0112, M20, -(m0210 * M21));
   r.r2 = fma(M01, X, -(M02 * m0221));
   r.r3 = fma(M01, fma(M21, s.d1, -m0120), M21 * m0221);
   r.r4 = fma(M12, fma(M02, s.d0, m0112), -(M02 * m0210));
@@ -179,7 +178,11 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
   const double t1 = s.d1 + s.d2;
   const double t2 = s.d0 - s.d2;
   const double t3 = -s.d0 - s.d1;
-  const double offdiag = fma(a01 * a12, a20, (a02 * a10) * a21);
+  // A01 A12 A20 + A02 A10 A21; the same two triple products give r1 of
+  // Algorithm 5 for A, and r1 for A^T is its negative (A10 A21 A02 - A20 A01 A12)
+  const double m0112 = a01 * a12, m0210 = a02 * a10;
+  const double q = m0210 * a21;
+  const double offdiag = fma(m0112, a20, q);
   const double mixed = fma(s.p01, t1, fma(s.p02, t2, s.p12 * t3));
   o.J3 = fma(-(t1 * t2), t3 * kInv27, fma(mixed, kInv3, offdiag));
   // Algorithm 5 (reading R1 for r10)
@@ -193,15 +196,17 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
   s.q12 = (s.p12 - s.p02) - d0d2;
   s.q13 = d0d2 + f0201;
   const double r14 = fma(s.d0, d1d2 - s.p01, fma(s.d1, s.p02, -(s.d2 * s.p12)));
-  const Dx u = dx13(a01, a02, a10, a12, a20, a21, s);
-  const Dx v = dx13(a10, a20, a01, a21, a02, a12, s);
+  const double r1 = fma(m0112, a20, -q);
+  const Dx u = dx13(a01, a02, a10, a12, a20, a21, m0112, m0210, s);
+  const Dx v = dx13(a10, a20, a01, a21, a02, a12, a10 * a21, a20 * a01, s);
   // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1), grouped by weight
   const double g6 = fma(u.r2, v.r2, fma(u.r3, v.r3, u.r4 * v.r4));
   const double g8 = fma(u.r5, v.r5, fma(u.r6, v.r6, u.r7 * v.r7));
   const double g2 = fma(u.r8, v.r8,
                         fma(u.r9, v.r9,
                             fma(u.r10, v.r10, fma(u.r11, v.r11, fma(u.r12, v.r12, u.r13 * v.r13)))));
-  o.D = fma(9.0 * u.r1, v.r1, fma(6.0, g6, fma(8.0, g8, fma(2.0, g2, r14 * r14))));
+  // w1 u1 v1 = 9 r1 (-r1)
+  o.D = fma(-9.0 * r1, r1, fma(6.0, g6, fma(8.0, g8, fma(2.0, g2, r14 * r14))));
   return o;
 }
 
