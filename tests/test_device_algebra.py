@@ -1,0 +1,350 @@
+"""The binary64 device source computes the paper's quantities, checked on the
+source text itself with exact (symbolic) arithmetic.
+
+The kernels regroup the paper's formulas into shared products and FMAs
+(Algorithms 2, 4 and 5, the trigonometric eigenvalues of Algorithm 6 in
+sine form, and the hand-written adjoint).  Here the statements of those device
+functions are read from ``csrc/eig3_f64.cuh``, translated to Python and run
+on sympy symbols, with fma(a, b, c) = a b + c, the reciprocal exact and the
+decimal constants replaced by the exact values they round.  Branches that
+only handle the exponent range or exact coalescence (power-of-two scalings,
+the cluster mean) are left out; everything else is the text the compiler
+sees.  The results must equal the definitions identically:
+
+  I1 = tr A,  J2 = tr(dev(A)^2)/2,  J3 = det dev(A),  Delta = 4 J2^3 - 27 J3^2,
+  the gradient = a_I1 dI1/dA + a_J2 dJ2/dA + a_J3 dJ3/dA, with a_J2, a_J3 the
+  derivatives of the roots of mu^3 - J2 mu - J3 (divided differences),
+  and lambda_k of the sine form the roots of that cubic.
+"""
+import math
+import os
+import re
+from decimal import Decimal, getcontext
+
+import pytest
+
+sp = pytest.importorskip("sympy")
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_2511_00292_gb300", "csrc", "eig3_f64.cuh")
+
+# exact values of the header's constants
+EXACT = {
+    "kInv3": sp.Rational(1, 3), "kInv6": sp.Rational(1, 6), "kInv9": sp.Rational(1, 9),
+    "kInv27": sp.Rational(1, 27), "kHalfSqrt3": sp.sqrt(3) / 2,
+    "kTwoOverSqrt3": 2 / sp.sqrt(3), "kK": 2 / (3 * sp.sqrt(3)),
+}
+
+
+class NS:
+    """A struct (Inv, Dx, Adj, ...): attributes set by the translated code."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+# ---------------------------------------------------------------------------
+# A translator for the C subset of these functions
+# ---------------------------------------------------------------------------
+
+def _source():
+    with open(SRC) as f:
+        return f.read()
+
+
+def _match(text, i, open_ch, close_ch):
+    depth = 0
+    for k in range(i, len(text)):
+        if text[k] == open_ch:
+            depth += 1
+        elif text[k] == close_ch:
+            depth -= 1
+            if depth == 0:
+                return k
+    raise ValueError("unbalanced")
+
+
+def _split_top(text, sep):
+    parts, depth, cur = [], 0, ""
+    for ch in text:
+        if ch in "([{":
+            depth += 1
+        elif ch in ")]}":
+            depth -= 1
+        if ch == sep and depth == 0:
+            parts.append(cur)
+            cur = ""
+        else:
+            cur += ch
+    parts.append(cur)
+    return parts
+
+
+def _definition(src, name):
+    m = re.search(r"__device__ __forceinline__ [\w:<>]+ " + name + r"\(", src)
+    assert m, name
+    p0 = m.end() - 1
+    p1 = _match(src, p0, "(", ")")
+    params = []
+    for p in _split_top(src[p0 + 1:p1], ","):
+        q = re.search(r"\(&(\w+)\)|&?(\w+)\s*$", p.strip())
+        params.append(q.group(1) or q.group(2))
+    b0 = src.index("{", p1)
+    b1 = _match(src, b0, "{", "}")
+    return params, src[b0 + 1:b1]
+
+
+def _statements(body):
+    body = re.sub(r"//[^\n]*", "", body)
+    body = "\n".join(l for l in body.split("\n") if not l.strip().startswith("#"))
+    out, i, n = [], 0, len(body)
+    while i < n:
+        while i < n and body[i].isspace():
+            i += 1
+        if i >= n:
+            break
+        m = re.match(r"(if|for)\s*\(", body[i:])
+        if m:  # control statement: skipped (range scaling, coalescence)
+            j = _match(body, i + m.end() - 1, "(", ")") + 1
+            while body[j].isspace():
+                j += 1
+            if body[j] == "{":
+                k = _match(body, j, "{", "}") + 1
+            else:
+                k = j
+                depth = 0
+                while not (body[k] == ";" and depth == 0):
+                    depth += body[k] in "([{"
+                    depth -= body[k] in ")]}"
+                    k += 1
+                k += 1
+            out.append(("ctrl", body[i:k]))
+            i = k
+            continue
+        k, depth = i, 0
+        while not (body[k] == ";" and depth == 0):
+            depth += body[k] in "([{"
+            depth -= body[k] in ")]}"
+            k += 1
+        out.append(("stmt", " ".join(body[i:k].split())))
+        i = k + 1
+    return out
+
+
+def _expr(e):
+    e = e.replace("{", "[").replace("}", "]")
+    e = re.sub(r"dev_scale<\d+>\(\w+\)", "0", e)
+    e = re.sub(r"(\w+)<\d+>\(", r"\1(", e)  # sqrt_nonneg<3>( and the like
+    e = re.sub(r"(?<![\w.])(\d+\.\d*)", lambda m: f"_Q('{m.group(1)}')", e)
+    t = re.match(r"^\s*(\w+)\s*\?\s*(.+?)\s*:\s*(.+)$", e)
+    if t:
+        e = f"(({t.group(2)}) if {t.group(1)} else ({t.group(3)}))"
+    return e
+
+
+TYPES = r"(double|int|bool|float|Adj|Adj3|Inv|Eig|Dx|DxShared)"
+
+
+def _translate(stmt):
+    if stmt.startswith("return "):
+        return "__ret__ = " + _expr(stmt[7:])
+    m = re.match(r"^(?:const )?" + TYPES + r"\s+(.*)$", stmt)
+    if m:
+        typ, rest = m.groups()
+        if typ in ("int", "bool"):  # exponent tests and coalescence flags: set by the caller
+            return ""
+        lines = []
+        for d in _split_top(rest, ","):
+            if "=" not in d:
+                lines.append(f"{d.strip()} = NS()")
+                continue
+            lhs, rhs = d.split("=", 1)
+            lines.append(f"{re.sub(r'\[\d+\]', '', lhs.strip())} = {_expr(rhs)}")
+        return "\n".join(lines)
+    m = re.match(r"^([\w.\[\]]+)\s*=(?!=)\s*(.*)$", stmt)
+    if not m:  # a call for its output arguments (the angle): left to the caller
+        return ""
+    return f"{m.group(1)} = {_expr(m.group(2))}"
+
+
+def device_function(name, **fixed):
+    """The device function `name` as a Python callable on sympy values.
+    `fixed` binds the names that integer/boolean statements would set."""
+    src = _source()
+    params, body = _definition(src, name)
+    code = "\n".join(_translate(s) for kind, s in _statements(body) if kind == "stmt")
+
+    def fn(*args):
+        env = dict(BASE_ENV)
+        env.update(fixed)
+        env.update(zip(params, args))
+        exec(code, env)
+        return env.get("__ret__")
+
+    fn.code = code
+    return fn
+
+
+BASE_ENV = dict(
+    _Q=sp.Rational, NS=NS, fma=lambda a, b, c: a * b + c,
+    recip_pos=lambda x: 1 / x, pow2d=lambda k: sp.Integer(2) ** k, **EXACT)
+BASE_ENV["dx13"] = lambda *a: device_function("dx13")(*a)
+
+
+# ---------------------------------------------------------------------------
+# Definitions
+# ---------------------------------------------------------------------------
+
+def invariants_of(A):
+    dev = A - A.trace() / 3 * sp.eye(3)
+    J2 = sp.expand((dev * dev).trace() / 2)
+    J3 = sp.expand(dev.det())
+    return sp.expand(A.trace()), J2, J3
+
+
+def general_symbols():
+    a = sp.symbols("a0:9", real=True)
+    return list(a), sp.Matrix(3, 3, a)
+
+
+def sym_symbols():
+    s = sp.symbols("s0:6", real=True)  # (A00, A11, A22, A12, A02, A01)
+    A = sp.Matrix([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+    return list(s), A
+
+
+def zero(expr):
+    return sp.expand(expr) == 0
+
+
+# ---------------------------------------------------------------------------
+# Tests
+# ---------------------------------------------------------------------------
+
+def test_constants_are_the_nearest_binary64_values():
+    src = _source()
+    getcontext().prec = 60
+    for name, exact in EXACT.items():
+        m = re.search(r"constexpr double " + name + r" = ([0-9.e+-]+);", src)
+        assert m, name
+        assert float(Decimal(m.group(1))) == float(sp.N(exact, 40)), name
+
+
+def test_invariants_general_source_equals_definitions():
+    """Algorithms 1, 2, 4 and 5 as regrouped for the FP64 pipe (shared
+    products, FMAs, r1 of dx(A^T) = -r1) are exactly I1, J2, J3 and the
+    discriminant."""
+    a, A = general_symbols()
+    o = device_function("invariants_general")(a)
+    I1, J2, J3 = invariants_of(A)
+    assert zero(o.I1 - I1)
+    assert zero(o.J2 - J2)
+    assert zero(o.J3 - J3)
+    assert zero(o.D - (4 * J2 ** 3 - 27 * J3 ** 2))
+
+
+def test_invariants_sym_source_equals_definitions():
+    s, A = sym_symbols()
+    o = device_function("invariants_sym")(s)
+    I1, J2, J3 = invariants_of(A)
+    assert zero(o.I1 - I1)
+    assert zero(o.J2 - J2)
+    assert zero(o.J3 - J3)
+    assert zero(o.D - (4 * J2 ** 3 - 27 * J3 ** 2))
+
+
+def test_delta_terms_carry_the_paper_weights():
+    """A plausible slip (a wrong weight of one product group, or r1 of dx(A^T)
+    taken with the wrong sign) breaks the identity above: the check is not
+    vacuous.  Altering one weight in the translated source must fail it."""
+    a, A = general_symbols()
+    fn = device_function("invariants_general")
+    src_code = fn.code
+    assert "_Q('8.0')" in src_code and "-_Q('9.0') * r1" in src_code
+    for old, new in (("_Q('8.0')", "_Q('6.0')"), ("-_Q('9.0') * r1", "_Q('9.0') * r1")):
+        env = dict(BASE_ENV)
+        env["a"] = a
+        exec(src_code.replace(old, new, 1), env)
+        o = env["__ret__"]
+        _, J2, J3 = invariants_of(A)
+        assert not zero(o.D - (4 * J2 ** 3 - 27 * J3 ** 2))
+
+
+def _roots_derivatives(r, s1, s2, g):
+    """mu_k of the sine form and a_J2 = sum g_k mu_k / p'(mu_k),
+    a_J3 = sum g_k / p'(mu_k) for p(mu) = mu^3 - J2 mu - J3."""
+    k = EXACT["kK"] * r
+    mu = [-k * (s2 + 2 * s1), k * (s1 - s2), k * (2 * s2 + s1)]
+    dp = [sp.Mul(*[mu[i] - mu[j] for j in range(3) if j != i]) for i in range(3)]
+    aJ3 = sum(g[i] / dp[i] for i in range(3))
+    aJ2 = sum(g[i] * mu[i] / dp[i] for i in range(3))
+    return mu, aJ2, aJ3
+
+
+def test_adjoint_scalars_source_are_root_derivatives():
+    """r a_J2 and r^2 a_J3 (divided differences over the gaps (2r/sqrt3) sigma)
+    are the derivatives of the roots of the depressed cubic, weighted by g."""
+    r, s1, s2 = sp.symbols("r sigma1 sigma2", positive=True)
+    g = sp.symbols("g1:4", real=True)
+    o = device_function("adjoint_scalars", z1=False, z2=False, rz=False, kr=0)(
+        r, s1, s2, *g)
+    _, aJ2, aJ3 = _roots_derivatives(r, s1, s2, g)
+    assert sp.simplify(o.aJ3r2 - r ** 2 * aJ3) == 0
+    assert sp.simplify(o.aJ2r - r * aJ2) == 0
+    assert sp.simplify(o.aI1 - sum(g) / 3) == 0
+    assert sp.simplify(o.inv_r - 1 / r) == 0
+
+
+def test_sine_form_eigenvalues_are_the_cubic_roots():
+    """lambda_k = I1/3 + mu_k of the source's sine form are the roots of
+    lambda^3 - I1 lambda^2 + ... for J2 = r^2/3 and J3 = (2 r^3/27) cos(3 psi)
+    with sigma1 = sin psi, sigma2 = sin(pi/3 - psi), and they ascend."""
+    I1, r, s1, s2 = sp.symbols("I1 r sigma1 sigma2", real=True)
+    fn = device_function("eigvals_from_inv")
+    code = "\n".join(l for l in fn.code.split("\n")
+                     if not re.match(r"\s*(o\.(j2_clamped|d_clamped|r) =|J2p|Dp|triple_angle_sines)", l))
+    env = dict(BASE_ENV)
+    env["v"] = NS(I1=I1)
+    env["o"] = NS(r=r, sigma1=s1, sigma2=s2)
+    exec(code.replace("o = NS()", ""), env)
+    o = env["__ret__"]
+    lam = [o.l1, o.l2, o.l3]
+    assert zero(sum(lam) - I1)
+    assert zero(lam[1] - lam[0] - 2 * r / sp.sqrt(3) * s1)     # gaps (2r/sqrt3) sigma
+    assert zero(lam[2] - lam[1] - 2 * r / sp.sqrt(3) * s2)
+    for psi in (0.0, 0.1, 0.37, math.pi / 6):
+        sub = {I1: sp.Rational(7, 5), r: sp.Rational(3, 2),
+               s1: sp.sin(sp.nsimplify(psi)), s2: sp.sin(sp.pi / 3 - sp.nsimplify(psi))}
+        J2 = sub[r] ** 2 / 3
+        J3 = 2 * sub[r] ** 3 / 27 * sp.cos(3 * sp.nsimplify(psi))
+        for lk in lam:
+            mu = lk.subs(sub) - sub[I1] / 3
+            assert abs(sp.N(mu ** 3 - J2 * mu - J3, 50)) < 1e-40
+
+
+def test_grad_general_source_is_the_chain_rule():
+    """G = a_I1 dI1/dA + a_J2 dJ2/dA + a_J3 dJ3/dA with a_J2 = (r a_J2) / r and
+    a_J3 = (r^2 a_J3) / r^2 (the source folds 1/r into the two weights)."""
+    a, A = general_symbols()
+    aI1, b2, b3, ir = sp.symbols("aI1 aJ2r aJ3r2 ir", real=True)
+    G = [None] * 9
+    device_function("grad_general")(a, NS(aI1=aI1, aJ2r=b2, aJ3r2=b3, inv_r=ir), G)
+    I1, J2, J3 = invariants_of(A)
+    for idx in range(9):
+        want = aI1 * sp.diff(I1, a[idx]) + b2 * ir * sp.diff(J2, a[idx]) + \
+            b3 * ir ** 2 * sp.diff(J3, a[idx])
+        assert zero(G[idx] - want), idx
+
+
+def test_grad_sym_source_is_the_chain_rule():
+    """The symmetric gradient is with respect to the six stored entries
+    (off-diagonal: G_ij + G_ji)."""
+    s, A = sym_symbols()
+    aI1, b2, b3, ir = sp.symbols("aI1 aJ2r aJ3r2 ir", real=True)
+    G = [None] * 6
+    device_function("grad_sym")(s, NS(aI1=aI1, aJ2r=b2, aJ3r2=b3, inv_r=ir), G)
+    I1, J2, J3 = invariants_of(A)
+    for idx in range(6):
+        want = aI1 * sp.diff(I1, s[idx]) + b2 * ir * sp.diff(J2, s[idx]) + \
+            b3 * ir ** 2 * sp.diff(J3, s[idx])
+        assert zero(G[idx] - want), idx
