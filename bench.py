@@ -49,9 +49,9 @@ WORKLOAD = ("mixed fwd+bwd, 2^28 matrices/GPU: 2^27 symmetric 6-entry FP32 (comp
 # They describe the kernel source whose hash is recorded here; when the source
 # changes they are reported as stale and the traffic as null.
 FWD_F64_COUNTERS = {
-    "source_md5": "9e7a181ebf10ffa71d428a0b1983b9e4",
-    "fp64_pipe_inst": 184.11, "dfma": 88.0, "dmul": 70.0, "dadd": 19.0,
-    "dram_bytes": (302.6176e6 + 193.16992e6) / 4194304,
+    "source_md5": "641a87d14bbce69e82c448ad064ec609",
+    "fp64_pipe_inst": 171.10, "dfma": 84.0, "dmul": 63.0, "dadd": 17.0,
+    "dram_bytes": (302.045184e6 + 192.892672e6) / 4194304,
 }
 FWD_F64_SOURCES = ("eig3_f64.cuh", "eig3_f64.cu", "eig3_stats.cuh", "eig3_tile.cuh")
 # FP64 pipe of GB300: 2 FMA lanes per SM (measured with a DFMA loop: 0.598 T

@@ -20,6 +20,7 @@ namespace eig3 {
 // Constants (binary64 nearest values).
 constexpr double kInv3 = 0.333333333333333314829616256247390992939472198486328125;
 constexpr double kInv6 = 0.1666666666666666574148081281236954964697360992431640625;
+constexpr double kInv9 = 0.111111111111111104943205418749130330979824066162109375;
 constexpr double kInv27 = 0.037037037037037034981127388472299207933247089385986328125;
 constexpr double kHalfSqrt3 = 0.86602540378443859658830206171842291951179504394531250;
 constexpr double kTwoOverSqrt3 = 1.1547005383792514621144972236652486026287078857421875;
@@ -67,6 +68,80 @@ __device__ __forceinline__ float seed_float(double x) {
 __device__ __forceinline__ double widen(float f) {
   const int b = __float_as_int(f);
   return ((b & 0x7f800000) == 0) ? 0.0 : __hiloint2double((b >> 3) + (896 << 20), b << 29);
+}
+
+// Binary32 reciprocal and reciprocal square root of a normal seed: one MUFU
+// instruction each (PTX rcp.approx / rsqrt.approx, relative error below
+// 2^-22), without the subnormal and special-value paths of the IEEE forms.
+__device__ __forceinline__ float rcp_seed(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float rsqrt_seed(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// seed_float(x 2^-s) and widen(f) 2^s for values outside the binary32 range:
+// the exponent is moved by integer arithmetic on the high word.  The caller
+// picks s so that the results stay in range; zero and subnormal x give 0.
+__device__ __forceinline__ float seed_float_scaled(double x, int s) {
+  const int hi = __double2hiint(x);
+  const int E = (hi >> 20) & 0x7ff;
+  const int e = E - s;
+  const int f = ((e - 896) << 23) | ((hi & 0xfffff) << 3) | (int)((unsigned)__double2loint(x) >> 29);
+  return (E == 0 || e < 897) ? 0.0f : __int_as_float(f);
+}
+
+__device__ __forceinline__ double widen_scaled(float f, int s) {
+  const int b = __float_as_int(f);
+  return ((b & 0x7f800000) == 0) ? 0.0 : __hiloint2double((b >> 3) + ((896 + s) << 20), b << 29);
+}
+
+// Square root and reciprocal from binary32 seeds, corrected by a truncated
+// binomial series in binary64.  The correction is a handful of FMAs on the
+// FP64 pipe; the seed, the exponent handling and the special cases run on the
+// FP32, MUFU and integer pipes.  Both are faithful (error below one unit in
+// the last place), not correctly rounded.
+//
+// sqrt(c x), x >= 0, c = 1 or 3: with x = 2^(2k) x', x' in [1, 4), and a
+// binary32 seed y0 ~ (c x')^(-1/2) (rsqrt_seed of the truncated c x': relative
+// error below 2^-21; for c = 3 rounded down to 22 significant bits, below
+// 2^-20, so that c y0 is exact in binary32),
+//   sqrt(c x') = g (1 - t)^(-1/2) = g (1 + t/2 + (3/8) t^2 + ...),  g = x' (c y0),  t = 1 - g y0,
+// truncated after t^2 (the next term is below 2^-60 g).  Forming t from the
+// rounded g cancels half of g's rounding error.  Zero and subnormal x give 0;
+// infinity and NaN pass through.
+template <int C = 1>
+__device__ __forceinline__ double sqrt_nonneg(double x) {
+  static_assert(C == 1 || C == 3, "factor 1 or 3");
+  const int hi = __double2hiint(x);
+  const int E = (hi >> 20) & 0x7ff;
+  const int k = (E - 1023) >> 1;
+  const double xs = __hiloint2double(hi - (k << 21), __double2loint(x));
+  float y0 = rsqrt_seed((float)C * seed_float(xs));
+  if (C == 3) y0 = __int_as_float(__float_as_int(y0) & ~3);
+  const double g = xs * widen((float)C * y0);
+  const double h = fma(-g, widen(0.5f * y0), 0.5);  // t / 2
+  const double s = fma(g * h, fma(1.5, h, 1.0), g);
+  const double r = __hiloint2double(__double2hiint(s) + (k << 20), __double2loint(s));
+  return (E == 0) ? 0.0 : ((E == 0x7ff) ? x : r);
+}
+
+// 1/x for positive normal x: with x = 2^k x', x' in [1, 2), the binary32
+// reciprocal c0 of the truncated x' (rcp_seed; e = 1 - x' c0 is below 2^-21)
+// and 1/x' = c0 / (1 - e) = c0 (1 + e + e^2 + ...), truncated after e^2.
+__device__ __forceinline__ double recip_pos(double x) {
+  const int hi = __double2hiint(x);
+  const int k = ((hi >> 20) & 0x7ff) - 1023;
+  const double xs = __hiloint2double(hi - (k << 20), __double2loint(x));
+  const double c0 = widen(rcp_seed(seed_float(xs)));
+  const double e = fma(-xs, c0, 1.0);
+  const double c = fma(c0, fma(e, e, e), c0);
+  return __hiloint2double(__double2hiint(c) - (k << 20), __double2loint(c));
 }
 
 // min of two non-negative doubles: their bit patterns order like their values.
@@ -174,7 +249,8 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
   s.p12 = a12 * a21;
   // Algorithm 2: diag/6 + offdiag
   o.J2 = fma(fma(s.d0, s.d0, fma(s.d1, s.d1, s.d2 * s.d2)), kInv6, (s.p01 + s.p02) + s.p12);
-  // Algorithm 4: offdiag + mixed/3 - t1 t2 t3 / 27
+  // Algorithm 4: offdiag + mixed/3 - t1 t2 t3 / 27, with mixed/3 - t1 t2 t3/27
+  // grouped as (1/3) [t1 (A01 A10 - t2 t3 / 9) + A02 A20 t2 + A12 A21 t3]
   const double t1 = s.d1 + s.d2;
   const double t2 = s.d0 - s.d2;
   const double t3 = -s.d0 - s.d1;
@@ -183,19 +259,19 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
   const double m0112 = a01 * a12, m0210 = a02 * a10;
   const double q = m0210 * a21;
   const double offdiag = fma(m0112, a20, q);
-  const double mixed = fma(s.p01, t1, fma(s.p02, t2, s.p12 * t3));
-  o.J3 = fma(-(t1 * t2), t3 * kInv27, fma(mixed, kInv3, offdiag));
-  // Algorithm 5 (reading R1 for r10)
-  const double d1d2 = s.d1 * s.d2;
-  const double d0d2 = s.d0 * s.d2;
+  const double u01 = fma(-t2, t3 * kInv9, s.p01);
+  o.J3 = fma(fma(t1, u01, fma(s.p02, t2, s.p12 * t3)), kInv3, offdiag);
+  // Algorithm 5 (reading R1 for r10).  The bracketed sums of r10 .. r14 are
+  // single FMAs (d1 d2 + (A02 A20 - A01 A10) and so on); p12 - p01 = -e8 and
+  // p12 - p02 = -e9 exactly.
   s.e8 = s.p01 - s.p12;
   s.e9 = s.p02 - s.p12;
   const double f0201 = s.p02 - s.p01;
-  s.q10 = d1d2 + f0201;
-  s.q11 = d1d2 + (s.p12 - s.p01);
-  s.q12 = (s.p12 - s.p02) - d0d2;
-  s.q13 = d0d2 + f0201;
-  const double r14 = fma(s.d0, d1d2 - s.p01, fma(s.d1, s.p02, -(s.d2 * s.p12)));
+  s.q10 = fma(s.d1, s.d2, f0201);
+  s.q11 = fma(s.d1, s.d2, -s.e8);
+  s.q12 = fma(-s.d0, s.d2, -s.e9);
+  s.q13 = fma(s.d0, s.d2, f0201);
+  const double r14 = fma(s.d0, fma(s.d1, s.d2, -s.p01), fma(s.d1, s.p02, -(s.d2 * s.p12)));
   const double r1 = fma(m0112, a20, -q);
   const Dx u = dx13(a01, a02, a10, a12, a20, a21, m0112, m0210, s);
   const Dx v = dx13(a10, a20, a01, a21, a02, a12, a10 * a21, a20 * a01, s);
@@ -230,20 +306,19 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
   o.J2 = fma(fma(d0, d0, fma(d1, d1, d2 * d2)), kInv6, (aa + bb) + cc);
   const double t1 = d1 + d2, t2 = d0 - d2, t3 = -d0 - d1;
   const double offdiag = 2.0 * (ab * c);
-  const double mixed = fma(aa, t1, fma(bb, t2, cc * t3));
-  o.J3 = fma(-(t1 * t2), t3 * kInv27, fma(mixed, kInv3, offdiag));
-  const double d1d2 = d1 * d2, d0d2 = d0 * d2;
-  const double fba = bb - aa;
+  const double uaa = fma(-t2, t3 * kInv9, aa);
+  o.J3 = fma(fma(t1, uaa, fma(bb, t2, cc * t3)), kInv3, offdiag);
+  const double fba = bb - aa, fac = aa - cc, fbc = bb - cc;
   const double r2 = fma(a, fma(-b, d2, ac), -(b * bc));
   const double r3 = fma(a, fma(c, d1, -ab), c * bc);
   const double r4 = fma(c, fma(b, d0, ac), -(b * ab));
-  const double r8 = fma(d1, fma(c, d0, -ab), c * (aa - cc));
-  const double r9 = fma(d0, fma(c, d1, -ab), c * (bb - cc));
-  const double r10 = fma(a, d1d2 + fba, d2 * bc);
-  const double r11 = fma(a, d1d2 + (cc - aa), d1 * bc);
-  const double r12 = fma(b, (cc - bb) - d0d2, d0 * ac);
-  const double r13 = fma(b, d0d2 + fba, d2 * ac);
-  const double r14 = fma(d0, d1d2 - aa, fma(d1, bb, -(d2 * cc)));
+  const double r8 = fma(d1, fma(c, d0, -ab), c * fac);
+  const double r9 = fma(d0, fma(c, d1, -ab), c * fbc);
+  const double r10 = fma(a, fma(d1, d2, fba), d2 * bc);
+  const double r11 = fma(a, fma(d1, d2, -fac), d1 * bc);
+  const double r12 = fma(b, fma(-d0, d2, -fbc), d0 * ac);
+  const double r13 = fma(b, fma(d0, d2, fba), d2 * ac);
+  const double r14 = fma(d0, fma(d1, d2, -aa), fma(d1, bb, -(d2 * cc)));
   const double g14 = fma(r2, r2, fma(r3, r3, r4 * r4));
   const double g2 =
       fma(r8, r8, fma(r9, r9, fma(r10, r10, fma(r11, r11, fma(r12, r12, r13 * r13)))));
@@ -276,13 +351,13 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
 __device__ __forceinline__ void triple_angle_sines(double x, double y, double &sigma1,
                                                    double &sigma2) {
   const double ax = fabs(x);
-  // 2^(1023 - e) with e the exponent field of max(|x|, y): scaled max in [1, 2)
+  // the seeds are taken from 2^-s |x| and 2^-s y, s the exponent of max(|x|, y),
+  // so that their maximum lies in [1, 2); the binary64 steps below use |x| and y
+  // themselves (|z| < 2^460 for the scaled deviatoric data)
   const int h = max(__double2hiint(ax), __double2hiint(y));
-  const int e = min((h >> 20) & 0x7ff, 2045);
-  const double sc = __hiloint2double((2046 - e) << 20, 0);
-  const double X = ax * sc, Y = y * sc;
+  const int s = min((h >> 20) & 0x7ff, 2045) - 1023;
   // binary32 seed w0 = c0 + i s0 (pf in [0, pi/6], so c0, s0 >= 0)
-  const float pf = atan2f(seed_float(Y), seed_float(X)) * (1.0f / 3.0f);
+  const float pf = atan2f(seed_float_scaled(y, s), seed_float_scaled(ax, s)) * (1.0f / 3.0f);
   float sf, cf;
   __sincosf(pf, &sf, &cf);
   const double c0 = widen(cf), s0 = widen(fmaxf(sf, 0.0f));
@@ -291,12 +366,16 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   const double a3 = c0 * fma(-3.0, ss, cc);
   const double b3 = s0 * fma(3.0, cc, -ss);
   // rho = z conj(w0^3); its argument is 3 eps (|3 eps| ~ 1e-6: arg = Im/Re to 1e-18)
-  const double re = fma(X, a3, Y * b3);
-  const double im = fma(Y, a3, -(X * b3));
-  const double rc0 = widen(__frcp_rn(seed_float(re)));
-  const double rc = fma(rc0, fma(-re, rc0, 1.0), rc0);
-  // z = 0 (re = +0): the angle is undetermined, keep phi = 0
-  const double eps = (__double2hiint(re) > 0) ? (im * rc) * kInv3 : 0.0;
+  const double re = fma(ax, a3, y * b3);
+  const double im = fma(y, a3, -(ax * b3));
+  // eps = im / (3 re): a binary32 seed rc0 of 1/(3 re) with 22 significant bits
+  // (so that 3 rc0 is exact) and one Newton step, rc0 (1 + e), e = 1 - 3 re rc0
+  const float rcf =
+      __int_as_float(__float_as_int(rcp_seed(seed_float_scaled(re, s)) * (1.0f / 3.0f)) & ~3);
+  const double rc0 = widen_scaled(rcf, -s);
+  const double e = fma(-re, widen_scaled(3.0f * rcf, -s), 1.0);
+  // z = 0 (or both |x| and y subnormal): the angle is undetermined, keep phi = 0
+  const double eps = (h >= (1 << 20)) ? im * fma(rc0, e, rc0) : 0.0;
   // 1/|w0| to second order in eta0 = |w0|^2 - 1 (|eta0| ~ 1e-7), folded into
   // the rotation w~ = w0 e^{i eps} / |w0| with e^{i eps} = 1 - eps^2/2 + i eps
   const double eta0 = (cc - 1.0) + ss;
@@ -331,10 +410,10 @@ __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
   o.d_clamped = negative(v.D);
   const double J2p = nonneg(v.J2);
   const double Dp = nonneg(v.D);
-  o.r = sqrt(3.0 * J2p);
+  o.r = sqrt_nonneg<3>(J2p);
   if (v.e != 0) o.r *= pow2d(v.e);
   // (J3, sqrt(Delta/27)) has the direction of (27 J3, sqrt(27 Delta))
-  triple_angle_sines(v.J3, sqrt(Dp * kInv27), o.sigma1, o.sigma2);
+  triple_angle_sines(v.J3, sqrt_nonneg(Dp * kInv27), o.sigma1, o.sigma2);
   const double k = o.r * kK;
   const double i3 = v.I1 * kInv3;
   o.l1 = fma(-k, fma(2.0, o.sigma1, o.sigma2), i3);
@@ -362,10 +441,11 @@ __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
 // 0, i.e. the cluster's weights are replaced by their mean; r = 0 (a triple
 // eigenvalue) leaves a_I1 I.
 //
-// Everything is carried in units of r: with S^ = dev(A)/r,
+// The scalars are carried in units of r: with S^ = dev(A)/r,
 //   a_J2 dev(A)^T = (r a_J2) S^T,   a_J3 dev(cof dev A) = (r^2 a_J3) dev(cof S^),
-// and r a_J2, r^2 a_J3 depend only on the sigmas and the weights, so no
-// intermediate over- or underflows for matrices of any scale.
+// and r a_J2, r^2 a_J3 depend only on the sigmas and the weights, so they
+// neither over- nor underflow for matrices of any scale; the gradient
+// routines below apply 1/r to S^ (symmetric) or to the scalars (general).
 // --------------------------------------------------------------------------
 struct Adj {
   double aI1, aJ2r, aJ3r2, inv_r;
@@ -378,7 +458,7 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const bool z2 = hi_abs(sigma2) < (63 << 20);
   const double s1 = z1 ? 1.0 : sigma1, s2 = z2 ? 1.0 : sigma2;
   const double s3 = sigma1 + sigma2;  // >= sin(pi/6) cos(pi/6): never 0
-  // One division serves all four reciprocals: with r = m 2^k, m in [1, 4),
+  // One reciprocal serves all four: with r = m 2^k, m in [1, 2),
   // and P = s1 s2 s3,  R = 1 / (m P) gives  1/r = P R 2^-k  and
   // (sqrt3/2)/s_i = (sqrt3/2) (P/s_i) (m R).  (The gaps in units of r are
   // (2/sqrt3) sigma1, (2/sqrt3) sigma2 and (2/sqrt3)(sigma1 + sigma2).)
@@ -389,12 +469,15 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const double m = rz ? 1.0 : r * p2k;
   const double s12 = s1 * s2;
   const double P = s12 * s3;
-  const double R = 1.0 / (m * P);
+  const double R = recip_pos(m * P);
   const double Rh = kHalfSqrt3 * (m * R);  // (sqrt3/2) / P
-  // an exactly coalesced pair takes the mean of its two weights
-  const double m12 = 0.5 * (g1 + g2), m23 = 0.5 * (g2 + g3);
-  const double D12 = z1 ? 0.0 : ((z2 ? m23 : g2) - g1) * ((s2 * s3) * Rh);
-  const double D23 = z2 ? 0.0 : (g3 - (z1 ? m12 : g2)) * ((s1 * s3) * Rh);
+  double n12 = g2 - g1, n23 = g3 - g2;
+  if (z1 || z2) {  // an exactly coalesced pair takes the mean of its two weights
+    n12 = z1 ? 0.0 : 0.5 * (g2 + g3) - g1;
+    n23 = z2 ? 0.0 : g3 - 0.5 * (g1 + g2);
+  }
+  const double D12 = n12 * ((s2 * s3) * Rh);
+  const double D23 = n23 * ((s1 * s3) * Rh);
   Adj o;
   o.aJ3r2 = (D23 - D12) * (s12 * Rh);
   o.aJ2r = fma(-kK * fma(2.0, sigma1, sigma2), o.aJ3r2, D23);
@@ -404,7 +487,7 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
 }
 
 // The adjoint scalars for the three unit weights e_1, e_2, e_3 at once (the
-// eigenprojectors), from the same single division: with X12 = (sqrt3/2)/s1,
+// eigenprojectors), from the same single reciprocal: with X12 = (sqrt3/2)/s1,
 // X23 = (sqrt3/2)/s2, X13 = (sqrt3/2)/s3 and c = -kK (2 sigma1 + sigma2), for
 // distinct eigenvalues
 //   e_1: r^2 a_J3 =  X12 X13,          r a_J2 = c (r^2 a_J3)
@@ -428,7 +511,7 @@ __device__ __forceinline__ Adj3 adjoint_units(double r, double sigma1, double si
   const double m = rz ? 1.0 : r * p2k;
   const double s12 = s1 * s2;
   const double P = s12 * s3;
-  const double R = 1.0 / (m * P);
+  const double R = recip_pos(m * P);
   const double Rh = kHalfSqrt3 * (m * R);
   const double X12 = (s2 * s3) * Rh;
   const double X23 = (s1 * s3) * Rh;
@@ -497,17 +580,30 @@ __device__ __forceinline__ void projectors(const double (&a)[N], const Adj3 &s, 
 }
 
 // Gradient of a general matrix from the adjoint scalars, G[0..8] row-major.
+// The powers of r go into the two weights instead of into the nine entries:
+//   (r a_J2) S^T = (r a_J2 / r) dev(A)^T,  (r^2 a_J3) dev cof S^ = (r^2 a_J3 / r^2) dev cof dev(A).
+// The products of dev(A) stay in range while its entries lie in [2^-448, 2^448];
+// outside, dev(A) is first multiplied by a power of two 2^-e (exact) and 1/r by 2^e.
 __device__ __forceinline__ void grad_general(const double (&a)[9], const Adj &s, double (&G)[9]) {
-  const double ir = s.inv_r;
   const double d0 = a[0] - a[4], d1 = a[0] - a[8], d2 = a[4] - a[8];
-  // S = dev(A) / r: diagonal from the differences, exact for A = alpha I
-  const double ir3 = ir * kInv3;
-  const double S00 = (d0 + d1) * ir3;
-  const double S11 = (d2 - d0) * ir3;
-  const double S22 = -(d1 + d2) * ir3;
-  const double S01 = a[1] * ir, S02 = a[2] * ir, S10 = a[3] * ir;
-  const double S12 = a[5] * ir, S20 = a[6] * ir, S21 = a[7] * ir;
-  // C = cof(S)
+  // dev(A): diagonal from the differences, exact for A = alpha I
+  double D[9] = {(d0 + d1) * kInv3, a[1], a[2], a[3], (d2 - d0) * kInv3, a[5], a[6], a[7],
+                 -(d1 + d2) * kInv3};
+  double ir = s.inv_r;
+  int h = hi_abs(D[0]);
+#pragma unroll
+  for (int j = 1; j < 9; ++j) h = max(h, hi_abs(D[j]));
+  const int E = h >> 20;
+  if (E < 1023 - 448 || E > 1023 + 448) {
+    const int e = min(max(E, 1), 2045) - 1023;
+    const double sc = pow2d(-e);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) D[j] *= sc;
+    ir *= pow2d(e);
+  }
+  const double S00 = D[0], S01 = D[1], S02 = D[2], S10 = D[3], S11 = D[4], S12 = D[5];
+  const double S20 = D[6], S21 = D[7], S22 = D[8];
+  // C = cof(dev A)
   const double C00 = fma(S11, S22, -(S12 * S21));
   const double C01 = fma(S12, S20, -(S10 * S22));
   const double C02 = fma(S10, S21, -(S11 * S20));
@@ -518,8 +614,8 @@ __device__ __forceinline__ void grad_general(const double (&a)[9], const Adj &s,
   const double C21 = fma(S02, S10, -(S00 * S12));
   const double C22 = fma(S00, S11, -(S01 * S10));
   const double tc = ((C00 + C11) + C22) * kInv3;
-  const double b2 = s.aJ2r, b3 = s.aJ3r2;
-  // G = aI1 I + (r aJ2) S^T + (r^2 aJ3) (C - tc I)
+  const double b2 = s.aJ2r * ir, b3 = (s.aJ3r2 * ir) * ir;
+  // G = aI1 I + a_J2 dev(A)^T + a_J3 (C - tc I)
   G[0] = fma(b2, S00, fma(b3, C00 - tc, s.aI1));
   G[1] = fma(b2, S10, b3 * C01);
   G[2] = fma(b2, S20, b3 * C02);

@@ -141,6 +141,30 @@ def test_power_of_two_scale_equivariance_f64(eig3, k):
         assert torch.equal(eig3.eigvals(X * 2.0 ** k), eig3.eigvals(X) * 2.0 ** k)
 
 
+def test_r_is_a_faithful_square_root(eig3):
+    """r = sqrt(3 J2+) (the first adjoint input) comes from a binary32 seed and a
+    series correction, not from the correctly rounded sqrt: it must lie within
+    one unit in the last place of the exact square root of 3 times the
+    kernel's own J2 (evaluated in extended precision), over a wide range of
+    exponents."""
+    bt = W.workload2(n=50_000, device="cpu", seed=1810)
+    g = torch.Generator().manual_seed(1811)
+    scale = 2.0 ** torch.randint(-120, 121, (bt.n, 1), generator=g).double()
+    A = torch.as_tensor(bt.A.numpy(), device=dev()) * scale.to(dev())
+    J2 = U.to_np(eig3.invariants(A))[:, 1]
+    _, aux = eig3.eigvals(A, return_aux=True)
+    r = U.to_np(aux)[:, 0]
+    pos = J2 > 0
+    assert pos.mean() > 0.9
+    ref = np.sqrt(np.longdouble(3.0) * J2[pos].astype(np.longdouble))
+    d = np.abs(r[pos].astype(np.longdouble) - ref)
+    ulp = np.spacing(r[pos]).astype(np.longdouble)
+    print(f"[edge] r: {np.mean(r[pos] == ref.astype(np.float64)):.3f} correctly rounded, "
+          f"max error {float(np.max(d / ulp)):.3f} ulp")
+    assert np.all(d < ulp)
+    assert np.all(r[~pos] == 0.0)
+
+
 @pytest.mark.parametrize("k", [-100, -40, 40, 100])
 def test_power_of_two_scale_equivariance_f32c(eig3, k):
     S = W.workload3(n=30_000, device="cpu", seed=1802).A
