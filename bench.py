@@ -493,15 +493,15 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
     start in pinned host memory and the eigenvalues and gradients end there;
     every host-to-device and device-to-host copy is inside the timed region,
     overlapped with the kernels chunk by chunk on separate streams."""
-    from paper_2511_00292_gb300.host import HostPipeline
-    hS = S.A.cpu().pin_memory()
-    hG = G.A.cpu().pin_memory()
-    hwS = S.extra["w"].cpu().pin_memory()
-    hwG = G.extra["w"].cpu().pin_memory()
-    olS = torch.empty(S.n, 3, dtype=torch.float32).pin_memory()
-    olG = torch.empty(G.n, 3, dtype=torch.float64).pin_memory()
-    ogS = torch.empty_like(hS).pin_memory()
-    ogG = torch.empty_like(hG).pin_memory()
+    from paper_2511_00292_gb300.host import HostPipeline, pinned_copy, pinned_empty
+    hS = pinned_copy(S.A)
+    hG = pinned_copy(G.A)
+    hwS = pinned_copy(S.extra["w"])
+    hwG = pinned_copy(G.extra["w"])
+    olS = pinned_empty((S.n, 3), torch.float32)
+    olG = pinned_empty((G.n, 3), torch.float64)
+    ogS = pinned_empty(hS.shape, hS.dtype)
+    ogG = pinned_empty(hG.shape, hG.dtype)
     h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
     d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
     pipe = HostPipeline(dev, chunk=1 << 21, depth=3)
@@ -519,7 +519,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
     # at once (host-to-device on one stream, device-to-host on another)
     nb = 1 << 30
     src_h = hG.view(-1).view(torch.uint8)[:nb]
-    dst_h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    dst_h = pinned_empty(nb, torch.uint8)
     dbuf = torch.empty(2, nb, dtype=torch.uint8, device=dev)
     s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
@@ -543,7 +543,8 @@ def measure_e2e(eig3, S, G, dev, stream, steps):
         bool(torch.equal(olS[:1024], eig3.eigvals(S.A[:1024], precision="f32c").cpu()))
     del hS, hG, hwS, hwG, olS, olG, ogS, ogG, pipe
     return {"value": (S.n + G.n) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "mode": "pinned host buffers, chunks of 2^21 streamed through 3 device slots "
+            "mode": "pinned host buffers (host.pinned_empty: huge-page mappings registered "
+                    "with CUDA), chunks of 2^21 streamed through 3 device slots "
                     "(H2D / kernels / D2H on 3 streams), captured once as a CUDA graph",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
             "results_match_device": ok,
@@ -559,7 +560,7 @@ def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
     import workloads as W
     oracle.build()
     threads = os.cpu_count() or 1
-    k = 1 << 23
+    k = 1 << 24  # 2 x 2^24 matrices: about 12 s of CPU time on 16 Grace cores
     iS = torch.as_tensor(W.sample_indices(S.n, k, seed=11), device=S.A.device)
     iG = torch.as_tensor(W.sample_indices(G.n, k, seed=12), device=G.A.device)
     S64 = S.A[iS].double().cpu().numpy()
@@ -585,7 +586,8 @@ def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
     cpu = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"{S64.shape[0]} symmetric + {G64.shape[0]} general matrices of the "
                      f"mixed workload, eigenvalues + eigenvector-form gradient, "
-                     f"{dt:.2f} s wall on {threads} threads",
+                     f"{dt:.2f} s wall on {threads} threads "
+                     f"(about {dt * threads:.0f} s of CPU time)",
            "single_thread_ns_per_matrix": ns_1t}
     err = {"f32c_sym6": float(np.max(eS / bS)), "f64_general9": float(np.max(eG / bG)),
            "bound": "kappa ||A||_F u (u = 2^-24 for f32c, 2^-53 for f64; C = 1)",

@@ -306,6 +306,37 @@ def test_zero_copy_pinned_host_buffers(eig3):
         eig3.eigvals(bt.A)          # pageable host memory is refused
 
 
+def test_huge_page_pinned_buffers(eig3):
+    """host.pinned_empty / pinned_copy (registered huge-page host memory) serve
+    the zero-copy path and HostPipeline with the device results bit for bit,
+    and dropping them releases their registration (allocating many in turn
+    keeps working)."""
+    from paper_2511_00292_gb300 import host
+    from paper_2511_00292_gb300.host import HostPipeline
+    bt = W.workload4(n=30_011, device="cpu", seed=2204)
+    hA, hw = host.pinned_copy(bt.A), host.pinned_copy(bt.extra["w"])
+    assert hA.is_pinned() and hw.is_pinned() and torch.equal(hA, bt.A)
+    dA = bt.A.to(dev())
+    l_d, a_d = eig3.eigvals(dA, return_aux=True)
+    g_d = eig3.eigvals_backward(dA, bt.extra["w"].to(dev()), aux=a_d)
+    lam_h = eig3.eigvals(hA, device=dev())
+    torch.cuda.synchronize()
+    assert torch.equal(lam_h, l_d.cpu())
+    lam = host.pinned_empty((bt.n, 3), torch.float64)
+    grad = host.pinned_empty(hA.shape, torch.float64)
+    HostPipeline(dev(), chunk=4096, depth=3).forward_backward(hA, hw, lam, grad)
+    torch.cuda.synchronize()
+    assert torch.equal(lam, l_d.cpu()) and torch.equal(grad, g_d.cpu())
+    for _ in range(8):
+        x = host.pinned_empty((1 << 24,), torch.float64)   # 128 MiB each
+        x[::4096].fill_(1.0)
+        y = torch.empty(1 << 24, dtype=torch.float64, device=dev())
+        y.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        del x, y
+    assert host.pinned_empty((0, 9)).shape == (0, 9)
+
+
 @pytest.mark.parametrize("depth", [2, 3])
 def test_host_pipeline_matches_device(eig3, depth):
     """Chunked host-to-device streaming gives the device results bit for bit,
