@@ -404,9 +404,11 @@ def measure_paths(eig3, W, dev, stream, steps):
     l3 = torch.empty(b3.n, 3, dtype=torch.float32, device=dev)
     tc = timed(lambda: eig3.eigvals(b3.A, precision="f32c", out=l3), steps, stream)
     td = timed(lambda: eig3.eigvals(b3.A, precision="f64", out=l3), steps, stream)
+    ta = timed(lambda: eig3.eigvals(b3.A, precision="f32c64", out=l3), steps, stream)
     paths["fwd_sym6_fp32_storage_2^27"] = {
         "f32c_G_matrices_per_s": b3.n / tc / 1e6, "f64_G_matrices_per_s": b3.n / td / 1e6,
-        "f32c_speedup_over_f64": td / tc}
+        "f32c_speedup_over_f64": td / tc,
+        "f32c64_G_matrices_per_s": b3.n / ta / 1e6}
     del b3, l3
     b4 = W.workload4(n=1 << 24, device=dev)
     lam4 = torch.empty(b4.n, 3, dtype=torch.float64, device=dev)

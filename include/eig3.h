@@ -45,7 +45,22 @@
  *                                  deviatoric part), binary32 out.  No binary64
  *                                  arithmetic on this path except the binary64
  *                                  invariants output of eig3_invariants.
- *  EIG3_F64 + EIG3_PREC_F32_COMP   rejected with EIG3_ERR_DTYPE.
+ *  EIG3_F32 + EIG3_PREC_F32_COMP_A64
+ *                                  as EIG3_PREC_F32_COMP, except that the final
+ *                                  combination of the compensated Delta and
+ *                                  27 J3 and the triple angle of Algorithm 6
+ *                                  are taken in binary64 for every matrix (the
+ *                                  sines rounded back to binary32).  It is
+ *                                  the upper end of any rule that takes these
+ *                                  steps in binary64 below a Delta/J2^3
+ *                                  threshold, and measures what binary64
+ *                                  there can buy.  Accepted by
+ *                                  eig3_eigvals and eig3_eigvals_backward (the
+ *                                  adjoint is the EIG3_PREC_F32_COMP one); the
+ *                                  other entry points reject it with
+ *                                  EIG3_ERR_DTYPE.
+ *  EIG3_F64 + EIG3_PREC_F32_COMP or EIG3_PREC_F32_COMP_A64
+ *                                  rejected with EIG3_ERR_DTYPE.
  *  EIG3_F64/F32 + EIG3_PREC_F64_GUARDED
  *                                  binary64 arithmetic with a guard for
  *                                  ill-conditioned eigenbases (where Sections
@@ -94,7 +109,12 @@ typedef enum {
 
 enum { EIG3_GENERAL9 = 0, EIG3_SYM6 = 1 };
 enum { EIG3_F64 = 0, EIG3_F32 = 1 };
-enum { EIG3_PREC_F64 = 0, EIG3_PREC_F32_COMP = 1, EIG3_PREC_F64_GUARDED = 2 };
+enum {
+  EIG3_PREC_F64 = 0,
+  EIG3_PREC_F32_COMP = 1,
+  EIG3_PREC_F64_GUARDED = 2,
+  EIG3_PREC_F32_COMP_A64 = 3
+};
 /* Invariant evaluations of eig3_eigvals_variant (the paper's comparisons). */
 enum { EIG3_VARIANT_PRESENT = 0, EIG3_VARIANT_NAIVE = 1, EIG3_VARIANT_NAIVE_TENSOR = 2 };
 

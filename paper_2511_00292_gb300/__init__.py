@@ -10,10 +10,12 @@ write directly over the host link (zero copy), and the library must be built.
 Layouts: ``"general9"`` (n, 9) row-major, or (n, 3, 3); ``"sym6"`` (n, 6) in
 the order (A00, A11, A22, A12, A02, A01).
 Precisions: ``"f64"`` (binary64 arithmetic; storage float64 or float32),
-``"f32c"`` (compensated binary32 arithmetic; storage float32) and ``"f64g"``
-(binary64 with the guard for ill-conditioned eigenbases: a strongly non-normal
-matrix gets its eigenvalues from the shifted QR algorithm instead of the
-closed form; eigenvalues and adjoint only).
+``"f32c"`` (compensated binary32 arithmetic; storage float32), ``"f32c64"``
+(the same with the final combination of Delta and the triple angle in binary64;
+eigenvalues and adjoint only) and ``"f64g"`` (binary64 with the guard for
+ill-conditioned eigenbases: a strongly non-normal matrix gets its eigenvalues
+from the shifted QR algorithm instead of the closed form; eigenvalues and
+adjoint only).
 
 Entry points: :func:`eigvals`, :func:`eigvals_backward`, :func:`eigvals_ad`
 (autograd), :func:`invariants`, :func:`eigprojectors`, :func:`mohr_coulomb`,
@@ -36,8 +38,10 @@ __all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojec
 
 _LAYOUTS = {"general9": GENERAL9, "sym6": SYM6, GENERAL9: GENERAL9, SYM6: SYM6}
 _PRECS = {"f64": PREC_F64, "f32c": PREC_F32_COMP, "f64g": _lib.PREC_F64_GUARDED,
+          "f32c64": _lib.PREC_F32_COMP_A64,
           PREC_F64: PREC_F64, PREC_F32_COMP: PREC_F32_COMP,
-          _lib.PREC_F64_GUARDED: _lib.PREC_F64_GUARDED}
+          _lib.PREC_F64_GUARDED: _lib.PREC_F64_GUARDED,
+          _lib.PREC_F32_COMP_A64: _lib.PREC_F32_COMP_A64}
 
 
 def layout_of(A: torch.Tensor, layout=None) -> int:

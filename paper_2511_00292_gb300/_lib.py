@@ -22,7 +22,7 @@ EXPORTS = (
 
 GENERAL9, SYM6 = 0, 1
 F64, F32 = 0, 1
-PREC_F64, PREC_F32_COMP, PREC_F64_GUARDED = 0, 1, 2
+PREC_F64, PREC_F32_COMP, PREC_F64_GUARDED, PREC_F32_COMP_A64 = 0, 1, 2, 3
 VARIANT_PRESENT, VARIANT_NAIVE, VARIANT_NAIVE_TENSOR = 0, 1, 2
 STATUS = {0: "EIG3_OK", 1: "EIG3_ERR_ARG", 2: "EIG3_ERR_LAYOUT", 3: "EIG3_ERR_DTYPE",
           4: "EIG3_ERR_ALIGN", 5: "EIG3_ERR_CUDA"}

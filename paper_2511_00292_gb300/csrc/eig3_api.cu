@@ -88,9 +88,11 @@ eig3_status check_modes(int layout, int dtype, int precision, int64_t n) {
   if (layout != EIG3_GENERAL9 && layout != EIG3_SYM6) return EIG3_ERR_LAYOUT;
   if (dtype != EIG3_F64 && dtype != EIG3_F32) return EIG3_ERR_DTYPE;
   if (precision != EIG3_PREC_F64 && precision != EIG3_PREC_F32_COMP &&
-      precision != EIG3_PREC_F64_GUARDED)
+      precision != EIG3_PREC_F64_GUARDED && precision != EIG3_PREC_F32_COMP_A64)
     return EIG3_ERR_DTYPE;
-  if (precision == EIG3_PREC_F32_COMP && dtype != EIG3_F32) return EIG3_ERR_DTYPE;
+  if ((precision == EIG3_PREC_F32_COMP || precision == EIG3_PREC_F32_COMP_A64) &&
+      dtype != EIG3_F32)
+    return EIG3_ERR_DTYPE;
   // n * 9 elements must be addressable with 64-bit offsets
   if (n < 0 || n > (INT64_MAX / 64)) return EIG3_ERR_ARG;
   return EIG3_OK;
@@ -106,7 +108,8 @@ eig3_status eig3_invariants(const void *A, int layout, int dtype, int precision,
                             double *inv, void *stream) {
   eig3_status st = check_modes(layout, dtype, precision, n);
   if (st != EIG3_OK) return st;
-  if (precision == EIG3_PREC_F64_GUARDED) return EIG3_ERR_DTYPE;
+  if (precision == EIG3_PREC_F64_GUARDED || precision == EIG3_PREC_F32_COMP_A64)
+    return EIG3_ERR_DTYPE;
   if (n == 0) return EIG3_OK;
   if (!A || !inv) return EIG3_ERR_ARG;
   if (!aligned(A, elem_size(dtype)) || !aligned(inv, 8)) return EIG3_ERR_ALIGN;
@@ -127,8 +130,9 @@ eig3_status eig3_eigvals(const void *A, int layout, int dtype, int precision, in
       (stats && !aligned(stats, 8)))
     return EIG3_ERR_ALIGN;
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == EIG3_PREC_F32_COMP)
-    return from_cuda(eig3::launch_eigvals_f32c(A, layout, n, lam, aux, stats, s));
+  if (precision == EIG3_PREC_F32_COMP || precision == EIG3_PREC_F32_COMP_A64)
+    return from_cuda(eig3::launch_eigvals_f32c(A, layout, n, lam, aux, stats,
+                                               precision == EIG3_PREC_F32_COMP_A64, s));
   if (precision == EIG3_PREC_F64_GUARDED && layout == EIG3_GENERAL9)
     return from_cuda(eig3::launch_eigvals_guarded(A, dtype, n, lam, aux, stats, s));
   return from_cuda(eig3::launch_eigvals_f64(A, layout, dtype, n, lam, aux, stats, s));
@@ -146,7 +150,7 @@ eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int prec
       (aux && !aligned(aux, es)))
     return EIG3_ERR_ALIGN;
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == EIG3_PREC_F32_COMP)
+  if (precision == EIG3_PREC_F32_COMP || precision == EIG3_PREC_F32_COMP_A64)
     return from_cuda(eig3::launch_backward_f32c(A, layout, n, grad_lam, aux, grad_A, s));
   // the guarded forward step only changes the adjoint inputs (r, sigma1,
   // sigma2): with aux given the binary64 adjoint is the same computation
@@ -159,7 +163,8 @@ eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precisi
                                void *lam, void *P, void *stream) {
   eig3_status st = check_modes(layout, dtype, precision, n);
   if (st != EIG3_OK) return st;
-  if (precision == EIG3_PREC_F64_GUARDED) return EIG3_ERR_DTYPE;
+  if (precision == EIG3_PREC_F64_GUARDED || precision == EIG3_PREC_F32_COMP_A64)
+    return EIG3_ERR_DTYPE;
   if (n == 0) return EIG3_OK;
   if (!A || !P) return EIG3_ERR_ARG;
   const size_t es = elem_size(dtype);
@@ -174,7 +179,8 @@ eig3_status eig3_mohr_coulomb(const void *sigma, int layout, int dtype, int prec
                               double s_yc, double m, void *f, void *grad_sigma, void *stream) {
   eig3_status st = check_modes(layout, dtype, precision, n);
   if (st != EIG3_OK) return st;
-  if (precision == EIG3_PREC_F64_GUARDED) return EIG3_ERR_DTYPE;
+  if (precision == EIG3_PREC_F64_GUARDED || precision == EIG3_PREC_F32_COMP_A64)
+    return EIG3_ERR_DTYPE;
   // S_yc and m are positive finite material constants (1/S_yc and m/S_yc
   // must be finite); checked before anything else is looked at.
   if (!(s_yc > 0.0) || !(m > 0.0) || !std::isfinite(s_yc) || !std::isfinite(m) ||
@@ -227,6 +233,6 @@ const char *eig3_status_string(int status) {
   }
 }
 
-int eig3_version(void) { return 10100; }
+int eig3_version(void) { return 10200; }
 
 }  // extern "C"

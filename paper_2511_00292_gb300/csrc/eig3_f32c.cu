@@ -62,7 +62,7 @@ __device__ __forceinline__ bool aligned16c(const void *p) {
   return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
 
-template <int LAYOUT, bool AUX, bool STATS>
+template <int LAYOUT, bool AUX, bool STATS, bool ANGLE64>
 __global__ void __launch_bounds__(kThreads)
     k_eigvals_c(const float *__restrict__ A, int64_t n, float *__restrict__ lam,
                 float *__restrict__ aux, eig3_stats *__restrict__ stats) {
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int j = 0; j < N; ++j) a[j] = row[j];
     const InvC v = invariants_c<LAYOUT, N>(a);
-    const EigC e = eigvals_c(v);
+    const EigC e = eigvals_c<ANGLE64>(v);
     lam[3 * i + 0] = e.l1;
     lam[3 * i + 1] = e.l2;
     lam[3 * i + 2] = e.l3;
@@ -204,23 +204,23 @@ cudaError_t inv_c(const void *A, int64_t n, double *inv, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int LAYOUT, bool AUX, bool STATS>
+template <int LAYOUT, bool AUX, bool STATS, bool ANGLE64>
 cudaError_t eig_c4(const void *A, int64_t n, void *lam, void *aux, eig3_stats *st,
                    cudaStream_t s) {
-  auto k = k_eigvals_c<LAYOUT, AUX, STATS>;
+  auto k = k_eigvals_c<LAYOUT, AUX, STATS, ANGLE64>;
   const int grid = grid_for((const void *)k, kThreads, 0, n);
   k<<<grid, kThreads, 0, s>>>((const float *)A, n, (float *)lam, (float *)aux, st);
   return cudaGetLastError();
 }
 
-template <int LAYOUT>
+template <int LAYOUT, bool ANGLE64>
 cudaError_t eig_c(const void *A, int64_t n, void *lam, void *aux, eig3_stats *st,
                   cudaStream_t s) {
   if (aux)
-    return st ? eig_c4<LAYOUT, true, true>(A, n, lam, aux, st, s)
-              : eig_c4<LAYOUT, true, false>(A, n, lam, aux, st, s);
-  return st ? eig_c4<LAYOUT, false, true>(A, n, lam, aux, st, s)
-            : eig_c4<LAYOUT, false, false>(A, n, lam, aux, st, s);
+    return st ? eig_c4<LAYOUT, true, true, ANGLE64>(A, n, lam, aux, st, s)
+              : eig_c4<LAYOUT, true, false, ANGLE64>(A, n, lam, aux, st, s);
+  return st ? eig_c4<LAYOUT, false, true, ANGLE64>(A, n, lam, aux, st, s)
+            : eig_c4<LAYOUT, false, false, ANGLE64>(A, n, lam, aux, st, s);
 }
 
 template <int LAYOUT, bool AUX>
@@ -249,9 +249,12 @@ cudaError_t launch_invariants_f32c(const void *A, int layout, int64_t n, double 
 }
 
 cudaError_t launch_eigvals_f32c(const void *A, int layout, int64_t n, void *lam, void *aux,
-                                eig3_stats *stats, cudaStream_t s) {
-  return layout == EIG3_GENERAL9 ? eig_c<EIG3_GENERAL9>(A, n, lam, aux, stats, s)
-                                 : eig_c<EIG3_SYM6>(A, n, lam, aux, stats, s);
+                                eig3_stats *stats, bool angle64, cudaStream_t s) {
+  if (angle64)
+    return layout == EIG3_GENERAL9 ? eig_c<EIG3_GENERAL9, true>(A, n, lam, aux, stats, s)
+                                   : eig_c<EIG3_SYM6, true>(A, n, lam, aux, stats, s);
+  return layout == EIG3_GENERAL9 ? eig_c<EIG3_GENERAL9, false>(A, n, lam, aux, stats, s)
+                                 : eig_c<EIG3_SYM6, false>(A, n, lam, aux, stats, s);
 }
 
 cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *lam, void *P,

@@ -1,6 +1,8 @@
 // eig3_f32c.cuh -- compensated binary32 evaluation of the invariants (I1, J2,
 // J3, Delta of Algorithms 1, 2, 4, 5) and of the eigenvalues (Algorithm 6),
-// one matrix per thread, no binary64 arithmetic.
+// one matrix per thread, with no binary64 arithmetic except in the optional
+// ANGLE64 form of eigvals_c (precision EIG3_PREC_F32_COMP_A64), which takes the
+// final combination of Delta and the triple angle in binary64.
 //
 // GB300 issues binary32 FMAs 64 times faster than binary64 ones, so this path
 // buys accuracy with extra binary32 operations instead:
@@ -21,6 +23,8 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "eig3_f64.cuh"  // triple_angle_sines, sqrt_nonneg (ANGLE64 only)
 
 namespace eig3 {
 namespace c32 {
@@ -348,6 +352,11 @@ struct EigC {
   bool j2_clamped, d_clamped;
 };
 
+// ANGLE64 (precision EIG3_PREC_F32_COMP_A64): the final combination of
+// Delta's and 27 J3's compensated pairs and the triple angle in binary64
+// (triple_angle_sines of the binary64 path, which needs the binary64 header),
+// rounded back to binary32 sines; everything else as in the binary32 path.
+template <bool ANGLE64 = false>
 __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
   EigC o;
   const float j2x6 = round1(v.J2x6);
@@ -357,16 +366,27 @@ __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
   const float p2e = unscale_pow2(v.e);
   // r = sqrt(3 J2) = sqrt(J2x6 / 2) * 2^e
   o.r = __fmul_rn(sqrtf(0.5f * fmaxf(j2x6, 0.0f)), p2e);
-  const float x = round1(v.J3x27);
-  const float y = sqrtf(27.0f * fmaxf(dd, 0.0f));
-  const float pt = atan2f(y, fabsf(x)) * (1.0f / 3.0f);
-  float st, ct;
-  sincos_small(pt, st, ct);
-  st = fmaxf(st, 0.0f);
-  const float other = fmaf(0.86602540378443864676f, ct, -0.5f * st);
-  const bool pos = !(x < 0.0f);
-  o.sigma1 = pos ? st : other;
-  o.sigma2 = pos ? other : st;
+  if constexpr (ANGLE64) {
+    const double x = (double)v.J3x27.s + (double)v.J3x27.c;
+    const double d = (double)v.D.s + (double)v.D.c;
+    o.d_clamped = d < 0.0;
+    double s1, s2;
+    // (27 J3, sqrt(27 Delta)) in the common scale of the compensated invariants
+    triple_angle_sines(x, sqrt_nonneg<3>(9.0 * nonneg(d)), s1, s2);
+    o.sigma1 = __double2float_rn(s1);
+    o.sigma2 = __double2float_rn(s2);
+  } else {
+    const float x = round1(v.J3x27);
+    const float y = sqrtf(27.0f * fmaxf(dd, 0.0f));
+    const float pt = atan2f(y, fabsf(x)) * (1.0f / 3.0f);
+    float st, ct;
+    sincos_small(pt, st, ct);
+    st = fmaxf(st, 0.0f);
+    const float other = fmaf(0.86602540378443864676f, ct, -0.5f * st);
+    const bool pos = !(x < 0.0f);
+    o.sigma1 = pos ? st : other;
+    o.sigma2 = pos ? other : st;
+  }
   o.I1 = round1(v.I1);
   const float k = o.r * 0.38490017945975050967f;
   const float i3 = __fdiv_rn(o.I1, 3.0f);

@@ -36,7 +36,7 @@ cudaError_t launch_backward_f64(const void *A, int layout, int dtype, int64_t n,
 cudaError_t launch_invariants_f32c(const void *A, int layout, int64_t n, double *inv,
                                    cudaStream_t s);
 cudaError_t launch_eigvals_f32c(const void *A, int layout, int64_t n, void *lam, void *aux,
-                                eig3_stats *stats, cudaStream_t s);
+                                eig3_stats *stats, bool angle64, cudaStream_t s);
 cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *lam, void *P,
                                    cudaStream_t s);
 cudaError_t launch_mohr_coulomb_f32c(const void *A, int layout, int64_t n, double s_yc, double m,

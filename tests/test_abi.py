@@ -49,7 +49,7 @@ def test_library_is_sm_103a_and_static_runtime():
 
 
 def test_version_and_status_strings(lib):
-    assert lib.eig3_version() == 10100
+    assert lib.eig3_version() == 10200
     assert lib.eig3_status_string(0) == b"EIG3_OK"
     for code in range(1, 6):
         assert lib.eig3_status_string(code).startswith(b"EIG3_ERR")
@@ -99,12 +99,21 @@ def test_host_validation_without_gpu(lib):
     assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 0, 5, None, bad_ptr, None) == 4
     assert lib.eig3_eigprojectors(ok_ptr, 2, 0, 0, 5, None, ok_ptr, None) == 2
     # the guarded precision: eigenvalues and adjoint only
-    assert lib.eig3_eigvals(ok_ptr, 0, 0, 3, 5, ok_ptr, None, None, None) == 3   # unknown
+    assert lib.eig3_eigvals(ok_ptr, 0, 0, 5, 5, ok_ptr, None, None, None) == 3   # unknown
     assert lib.eig3_eigprojectors(ok_ptr, 0, 0, 2, 5, None, ok_ptr, None) == 3
     assert lib.eig3_invariants(ok_ptr, 0, 0, 2, 5, ok_ptr, None) == 3
     assert lib.eig3_mohr_coulomb(ok_ptr, 1, 0, 2, 5, ctypes.c_double(100.0),
                                  ctypes.c_double(10.0), ok_ptr, None, None) == 3
     assert lib.eig3_eigvals(bad_ptr, 0, 0, 2, 5, ok_ptr, None, None, None) == 4
+    # compensated binary32 with the binary64 angle: binary32 storage, eigenvalues and
+    # adjoint only (an alignment error shows that a call got past the mode checks)
+    assert lib.eig3_eigvals(ok_ptr, 1, 0, 3, 5, ok_ptr, None, None, None) == 3    # F64 storage
+    assert lib.eig3_eigvals(bad_ptr, 1, 1, 3, 5, ok_ptr, None, None, None) == 4
+    assert lib.eig3_eigvals_backward(bad_ptr, 1, 1, 3, 5, ok_ptr, None, ok_ptr, None) == 4
+    assert lib.eig3_invariants(ok_ptr, 1, 1, 3, 5, ok_ptr, None) == 3
+    assert lib.eig3_eigprojectors(ok_ptr, 1, 1, 3, 5, None, ok_ptr, None) == 3
+    assert lib.eig3_mohr_coulomb(ok_ptr, 1, 1, 3, 5, ctypes.c_double(100.0),
+                                 ctypes.c_double(10.0), ok_ptr, None, None) == 3
     # Mohr-Coulomb: material constants are checked first
     D = ctypes.c_double
     mc = lib.eig3_mohr_coulomb

@@ -126,6 +126,44 @@ def test_workload3_f32c_path(eig3):
     assert np.all(np.diff(lam, axis=1) >= 0)
 
 
+def test_workload3_f32c_angle64_by_disc_ratio(eig3):
+    """The compensated binary32 path with the final Delta combination and the
+    triple angle in binary64 (precision "f32c64") beside the plain one, per bin
+    of Delta/J2^3 = 4 sin^2(phi) taken from the oracle's eigenvalues: both stay
+    within the compensated tolerance in every bin, and the per-bin maxima (in
+    ulp of max|lambda|) show what binary64 buys where (the measured threshold
+    of the north-star's selective binary64 angle)."""
+    bt = W.workload3(n=200_003, device="cpu", seed=1305)
+    A = bt.A.to(dev())
+    lam32 = U.to_np(eig3.eigvals(A, precision="f32c"))
+    lam64, aux64 = eig3.eigvals(A, precision="f32c64", return_aux=True)
+    A64 = bt.A.double().numpy()
+    e32, tol, u32 = U.check_eig_f32c(lam32, A64, 1.0, SYM)
+    e64, _, u64 = U.check_eig_f32c(U.to_np(lam64), A64, 1.0, SYM)
+    assert np.all(e32 <= tol) and np.all(e64 <= tol)
+    assert np.all(np.diff(U.to_np(lam64), axis=1) >= 0)
+    ref = np.sort(oracle.eigvals(A64, layout=SYM), axis=1)
+    g12, g23 = ref[:, 1] - ref[:, 0], ref[:, 2] - ref[:, 1]
+    j2 = (g12 * g12 + g12 * g23 + g23 * g23) / 3.0
+    ratio = (g12 * g23 * (g12 + g23)) ** 2 / np.maximum(j2, 1e-300) ** 3
+    edges = [0.0, 1e-8, 1e-6, 1e-4, 1e-2, 1.0, 5.0]
+    rows = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        m = (ratio >= lo) & (ratio < hi)
+        if m.any():
+            rows.append(f"[{lo:g},{hi:g}) n={int(m.sum())} f32c {u32[m].max():.2f} "
+                        f"f32c64 {u64[m].max():.2f}")
+    report("w3 f32c vs f32c64 max ulp by Delta/J2^3", bins="; ".join(rows))
+    # the adjoint takes the binary64-angle adjoint inputs like the compensated ones
+    w = torch.randn(bt.n, 3, dtype=torch.float32, device=dev())
+    g64 = eig3.eigvals_backward(A, w, aux=aux64, precision="f32c64")
+    g32 = eig3.eigvals_backward(A, w, precision="f32c")
+    assert bool(torch.isfinite(g64).all())
+    sep = torch.as_tensor(np.minimum(g12, g23) / np.abs(ref).max(axis=1) > 1e-2, device=dev())
+    rel = ((g64 - g32).abs().amax(dim=1) / g32.abs().amax(dim=1).clamp_min(1e-30))[sep]
+    assert float(rel.max()) < 1e-3
+
+
 def test_workload3_f32c_invariants(eig3):
     bt = W.workload3(n=50_001, device="cpu", seed=1304)
     A = bt.A.to(dev())
