@@ -441,14 +441,16 @@ __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
 // 0, i.e. the cluster's weights are replaced by their mean; r = 0 (a triple
 // eigenvalue) leaves a_I1 I.
 //
-// The scalars are carried in units of r: with S^ = dev(A)/r,
-//   a_J2 dev(A)^T = (r a_J2) S^T,   a_J3 dev(cof dev A) = (r^2 a_J3) dev(cof S^),
-// and r a_J2, r^2 a_J3 depend only on the sigmas and the weights, so they
-// neither over- nor underflow for matrices of any scale; the gradient
-// routines below apply 1/r to S^ (symmetric) or to the scalars (general).
+// With r = m 2^k (m in [1, 2)) the scalars are carried as a_J2 2^k and
+// a_J3 2^2k: these depend only on m, the sigmas and the weights, so they
+// neither over- nor underflow for matrices of any scale, and the gradient
+// routines apply 2^-k and 2^-2k exactly (or, out of range, 2^-k to dev(A)).
+// One reciprocal R = 1/(m P), P = s1 s2 s3, serves every divided difference.
 // --------------------------------------------------------------------------
 struct Adj {
-  double aI1, aJ2r, aJ3r2, inv_r;
+  double aI1, aJ2s, aJ3s;  // a_I1, a_J2 2^k, a_J3 2^2k
+  int k;                   // r = m 2^k; 0 when r = 0
+  bool rz;                 // r = 0 (or subnormal): a triple eigenvalue, a_J2 = a_J3 = 0
 };
 
 __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double sigma2, double g1,
@@ -458,10 +460,9 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const bool z2 = hi_abs(sigma2) < (63 << 20);
   const double s1 = z1 ? 1.0 : sigma1, s2 = z2 ? 1.0 : sigma2;
   const double s3 = sigma1 + sigma2;  // >= sin(pi/6) cos(pi/6): never 0
-  // One reciprocal serves all four: with r = m 2^k, m in [1, 2),
-  // and P = s1 s2 s3,  R = 1 / (m P) gives  1/r = P R 2^-k  and
-  // (sqrt3/2)/s_i = (sqrt3/2) (P/s_i) (m R).  (The gaps in units of r are
-  // (2/sqrt3) sigma1, (2/sqrt3) sigma2 and (2/sqrt3)(sigma1 + sigma2).)
+  // The gaps are (2r/sqrt3) sigma1, (2r/sqrt3) sigma2 and (2r/sqrt3)(sigma1 +
+  // sigma2); with Rh = (sqrt3/2) / (P m), P = s1 s2 s3, their reciprocals
+  // times 2^k are (s2 s3) Rh, (s1 s3) Rh and (s1 s2) Rh.
   const int hr = hi_abs(r);
   const bool rz = hr < (1 << 20);  // r = 0 or subnormal: a triple eigenvalue
   const int kr = min((hr >> 20) - 1023, 1022);
@@ -470,7 +471,7 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const double s12 = s1 * s2;
   const double P = s12 * s3;
   const double R = recip_pos(m * P);
-  const double Rh = kHalfSqrt3 * (m * R);  // (sqrt3/2) / P
+  const double Rh = kHalfSqrt3 * R;
   double n12 = g2 - g1, n23 = g3 - g2;
   if (z1 || z2) {  // an exactly coalesced pair takes the mean of its two weights
     n12 = z1 ? 0.0 : 0.5 * (g2 + g3) - g1;
@@ -478,11 +479,15 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   }
   const double D12 = n12 * ((s2 * s3) * Rh);
   const double D23 = n23 * ((s1 * s3) * Rh);
+  const double aJ3s = (D23 - D12) * (s12 * Rh);
+  // mu1 2^-k = -kK m (2 sigma1 + sigma2)
+  const double aJ2s = fma((-kK * m) * fma(2.0, sigma1, sigma2), aJ3s, D23);
   Adj o;
-  o.aJ3r2 = (D23 - D12) * (s12 * Rh);
-  o.aJ2r = fma(-kK * fma(2.0, sigma1, sigma2), o.aJ3r2, D23);
   o.aI1 = ((g1 + g2) + g3) * kInv3;
-  o.inv_r = rz ? 0.0 : (P * R) * p2k;
+  o.aJ2s = rz ? 0.0 : aJ2s;
+  o.aJ3s = rz ? 0.0 : aJ3s;
+  o.k = rz ? 0 : kr;
+  o.rz = rz;
   return o;
 }
 
@@ -579,31 +584,40 @@ __device__ __forceinline__ void projectors(const double (&a)[N], const Adj3 &s, 
   }
 }
 
-// Gradient of a general matrix from the adjoint scalars, G[0..8] row-major.
-// The powers of r go into the two weights instead of into the nine entries:
-//   (r a_J2) S^T = (r a_J2 / r) dev(A)^T,  (r^2 a_J3) dev cof S^ = (r^2 a_J3 / r^2) dev cof dev(A).
-// The products of dev(A) stay in range while its entries lie in [2^-448, 2^448];
-// outside, dev(A) is first multiplied by a power of two 2^-e (exact) and 1/r by 2^e.
+// The gradient weights from b2 = a_J2 2^k and b3 = a_J3 2^2k (in place):
+// while r and the entries of dev(A) lie in [2^-448, 2^448], b2 *= 2^-k and
+// b3 *= 2^-2k (exact) and dev(A) is used as it is; otherwise dev(A) is
+// multiplied by 2^-k instead (exact; zero for r = 0, where b2 = b3 = 0), so
+// that its products stay in range.  Every term of the gradient is the same
+// either way.
+template <int N>
+__device__ __forceinline__ void grad_units(double (&D)[N], const Adj &s, double &b2, double &b3) {
+  int h = hi_abs(D[0]);
+#pragma unroll
+  for (int j = 1; j < N; ++j) h = max(h, hi_abs(D[j]));
+  const int E = h >> 20;
+  if (E >= 1023 - 448 && E <= 1023 + 448 && s.k >= -448 && s.k <= 448) {
+    b2 *= pow2d(-s.k);
+    b3 *= pow2d(-2 * s.k);
+  } else {
+    const double sc = s.rz ? 0.0 : pow2d(-s.k);
+#pragma unroll
+    for (int j = 0; j < N; ++j) D[j] *= sc;
+  }
+}
+
+// Gradient of a general matrix from the adjoint scalars, G[0..8] row-major:
+//   G = a_I1 I + a_J2 dev(A)^T + a_J3 (C - tr(C)/3 I),  C = cof(dev A),
+// the diagonal written as (a_I1 - a_J3 tr(C)/3) + a_J2 dev(A)_ii + a_J3 C_ii.
 __device__ __forceinline__ void grad_general(const double (&a)[9], const Adj &s, double (&G)[9]) {
   const double d0 = a[0] - a[4], d1 = a[0] - a[8], d2 = a[4] - a[8];
   // dev(A): diagonal from the differences, exact for A = alpha I
   double D[9] = {(d0 + d1) * kInv3, a[1], a[2], a[3], (d2 - d0) * kInv3, a[5], a[6], a[7],
                  -(d1 + d2) * kInv3};
-  double ir = s.inv_r;
-  int h = hi_abs(D[0]);
-#pragma unroll
-  for (int j = 1; j < 9; ++j) h = max(h, hi_abs(D[j]));
-  const int E = h >> 20;
-  if (E < 1023 - 448 || E > 1023 + 448) {
-    const int e = min(max(E, 1), 2045) - 1023;
-    const double sc = pow2d(-e);
-#pragma unroll
-    for (int j = 0; j < 9; ++j) D[j] *= sc;
-    ir *= pow2d(e);
-  }
+  double b2 = s.aJ2s, b3 = s.aJ3s;
+  grad_units<9>(D, s, b2, b3);
   const double S00 = D[0], S01 = D[1], S02 = D[2], S10 = D[3], S11 = D[4], S12 = D[5];
   const double S20 = D[6], S21 = D[7], S22 = D[8];
-  // C = cof(dev A)
   const double C00 = fma(S11, S22, -(S12 * S21));
   const double C01 = fma(S12, S20, -(S10 * S22));
   const double C02 = fma(S10, S21, -(S11 * S20));
@@ -613,43 +627,38 @@ __device__ __forceinline__ void grad_general(const double (&a)[9], const Adj &s,
   const double C20 = fma(S01, S12, -(S02 * S11));
   const double C21 = fma(S02, S10, -(S00 * S12));
   const double C22 = fma(S00, S11, -(S01 * S10));
-  const double tc = ((C00 + C11) + C22) * kInv3;
-  const double b2 = s.aJ2r * ir, b3 = (s.aJ3r2 * ir) * ir;
-  // G = aI1 I + a_J2 dev(A)^T + a_J3 (C - tc I)
-  G[0] = fma(b2, S00, fma(b3, C00 - tc, s.aI1));
+  const double base = fma(-b3, ((C00 + C11) + C22) * kInv3, s.aI1);
+  G[0] = fma(b2, S00, fma(b3, C00, base));
   G[1] = fma(b2, S10, b3 * C01);
   G[2] = fma(b2, S20, b3 * C02);
   G[3] = fma(b2, S01, b3 * C10);
-  G[4] = fma(b2, S11, fma(b3, C11 - tc, s.aI1));
+  G[4] = fma(b2, S11, fma(b3, C11, base));
   G[5] = fma(b2, S21, b3 * C12);
   G[6] = fma(b2, S02, b3 * C20);
   G[7] = fma(b2, S12, b3 * C21);
-  G[8] = fma(b2, S22, fma(b3, C22 - tc, s.aI1));
+  G[8] = fma(b2, S22, fma(b3, C22, base));
 }
 
 // Gradient with respect to the six stored entries of a symmetric matrix:
-// diagonal G_ii, off-diagonal G_ij + G_ji = 2 (aJ2 S_ij + aJ3 C_ij) (S and
-// cof(S) are symmetric).  Output order (A00, A11, A22, A12, A02, A01).
+// diagonal G_ii, off-diagonal G_ij + G_ji = 2 (a_J2 S_ij + a_J3 C_ij) (S =
+// dev(A) and cof(S) are symmetric).  Output order (A00, A11, A22, A12, A02, A01).
 __device__ __forceinline__ void grad_sym(const double (&s6)[6], const Adj &s, double (&G)[6]) {
-  const double ir = s.inv_r;
   const double d0 = s6[0] - s6[1], d1 = s6[0] - s6[2], d2 = s6[1] - s6[2];
-  const double ir3 = ir * kInv3;
-  const double S00 = (d0 + d1) * ir3;
-  const double S11 = (d2 - d0) * ir3;
-  const double S22 = -(d1 + d2) * ir3;
-  const double S12 = s6[3] * ir, S02 = s6[4] * ir, S01 = s6[5] * ir;
+  double D[6] = {(d0 + d1) * kInv3, (d2 - d0) * kInv3, -(d1 + d2) * kInv3, s6[3], s6[4], s6[5]};
+  double b2 = s.aJ2s, b3 = s.aJ3s;
+  grad_units<6>(D, s, b2, b3);
+  const double S00 = D[0], S11 = D[1], S22 = D[2], S12 = D[3], S02 = D[4], S01 = D[5];
   const double C00 = fma(S11, S22, -(S12 * S12));
   const double C11 = fma(S00, S22, -(S02 * S02));
   const double C22 = fma(S00, S11, -(S01 * S01));
   const double C12 = fma(S01, S02, -(S00 * S12));
   const double C02 = fma(S01, S12, -(S02 * S11));
   const double C01 = fma(S12, S02, -(S01 * S22));
-  const double tc = ((C00 + C11) + C22) * kInv3;
-  const double b2 = s.aJ2r, b3 = s.aJ3r2;
+  const double base = fma(-b3, ((C00 + C11) + C22) * kInv3, s.aI1);
   const double b2x2 = 2.0 * b2, b3x2 = 2.0 * b3;
-  G[0] = fma(b2, S00, fma(b3, C00 - tc, s.aI1));
-  G[1] = fma(b2, S11, fma(b3, C11 - tc, s.aI1));
-  G[2] = fma(b2, S22, fma(b3, C22 - tc, s.aI1));
+  G[0] = fma(b2, S00, fma(b3, C00, base));
+  G[1] = fma(b2, S11, fma(b3, C11, base));
+  G[2] = fma(b2, S22, fma(b3, C22, base));
   G[3] = fma(b2x2, S12, b3x2 * C12);
   G[4] = fma(b2x2, S02, b3x2 * C02);
   G[5] = fma(b2x2, S01, b3x2 * C01);

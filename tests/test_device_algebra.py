@@ -282,17 +282,18 @@ def _roots_derivatives(r, s1, s2, g):
 
 
 def test_adjoint_scalars_source_are_root_derivatives():
-    """r a_J2 and r^2 a_J3 (divided differences over the gaps (2r/sqrt3) sigma)
-    are the derivatives of the roots of the depressed cubic, weighted by g."""
+    """a_J2 2^k and a_J3 2^2k (divided differences over the gaps (2r/sqrt3)
+    sigma, r = m 2^k; here k = 0) are the derivatives of the roots of the
+    depressed cubic, weighted by g."""
     r, s1, s2 = sp.symbols("r sigma1 sigma2", positive=True)
     g = sp.symbols("g1:4", real=True)
     o = device_function("adjoint_scalars", z1=False, z2=False, rz=False, kr=0)(
         r, s1, s2, *g)
     _, aJ2, aJ3 = _roots_derivatives(r, s1, s2, g)
-    assert sp.simplify(o.aJ3r2 - r ** 2 * aJ3) == 0
-    assert sp.simplify(o.aJ2r - r * aJ2) == 0
+    assert sp.simplify(o.aJ3s - aJ3) == 0
+    assert sp.simplify(o.aJ2s - aJ2) == 0
     assert sp.simplify(o.aI1 - sum(g) / 3) == 0
-    assert sp.simplify(o.inv_r - 1 / r) == 0
+    assert o.k == 0 and o.rz is False
 
 
 def test_sine_form_eigenvalues_are_the_cubic_roots():
@@ -323,16 +324,15 @@ def test_sine_form_eigenvalues_are_the_cubic_roots():
 
 
 def test_grad_general_source_is_the_chain_rule():
-    """G = a_I1 dI1/dA + a_J2 dJ2/dA + a_J3 dJ3/dA with a_J2 = (r a_J2) / r and
-    a_J3 = (r^2 a_J3) / r^2 (the source folds 1/r into the two weights)."""
+    """G = a_I1 dI1/dA + a_J2 dJ2/dA + a_J3 dJ3/dA (the scalars at k = 0,
+    where the exact power-of-two unit changes leave them as they are)."""
     a, A = general_symbols()
-    aI1, b2, b3, ir = sp.symbols("aI1 aJ2r aJ3r2 ir", real=True)
+    aI1, b2, b3 = sp.symbols("aI1 aJ2 aJ3", real=True)
     G = [None] * 9
-    device_function("grad_general")(a, NS(aI1=aI1, aJ2r=b2, aJ3r2=b3, inv_r=ir), G)
+    device_function("grad_general")(a, NS(aI1=aI1, aJ2s=b2, aJ3s=b3, k=0, rz=False), G)
     I1, J2, J3 = invariants_of(A)
     for idx in range(9):
-        want = aI1 * sp.diff(I1, a[idx]) + b2 * ir * sp.diff(J2, a[idx]) + \
-            b3 * ir ** 2 * sp.diff(J3, a[idx])
+        want = aI1 * sp.diff(I1, a[idx]) + b2 * sp.diff(J2, a[idx]) + b3 * sp.diff(J3, a[idx])
         assert zero(G[idx] - want), idx
 
 
@@ -340,11 +340,10 @@ def test_grad_sym_source_is_the_chain_rule():
     """The symmetric gradient is with respect to the six stored entries
     (off-diagonal: G_ij + G_ji)."""
     s, A = sym_symbols()
-    aI1, b2, b3, ir = sp.symbols("aI1 aJ2r aJ3r2 ir", real=True)
+    aI1, b2, b3 = sp.symbols("aI1 aJ2 aJ3", real=True)
     G = [None] * 6
-    device_function("grad_sym")(s, NS(aI1=aI1, aJ2r=b2, aJ3r2=b3, inv_r=ir), G)
+    device_function("grad_sym")(s, NS(aI1=aI1, aJ2s=b2, aJ3s=b3, k=0, rz=False), G)
     I1, J2, J3 = invariants_of(A)
     for idx in range(6):
-        want = aI1 * sp.diff(I1, s[idx]) + b2 * ir * sp.diff(J2, s[idx]) + \
-            b3 * ir ** 2 * sp.diff(J3, s[idx])
+        want = aI1 * sp.diff(I1, s[idx]) + b2 * sp.diff(J2, s[idx]) + b3 * sp.diff(J3, s[idx])
         assert zero(G[idx] - want), idx
