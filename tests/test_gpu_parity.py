@@ -195,10 +195,12 @@ def test_workload3_full_size_sampled(eig3):
     torch.cuda.empty_cache()
 
 
-def test_general9_f32c(eig3):
+@pytest.mark.parametrize("prec", ["f32c", "f32c64"])
+def test_general9_f32c(eig3, prec):
     bt = W.workload2(n=60_001, device="cpu", seed=1305)
     A32 = bt.A.float()
-    lam = U.to_np(eig3.eigvals(A32.to(dev()), precision="f32c"))
+    lam = U.to_np(eig3.eigvals(A32.to(dev()), precision=prec))
     err, tol, ulps = U.check_eig_f32c(lam, A32.double().numpy(), bt.kappa.numpy(), GEN, c32=16.0)
-    report("general9 f32c", max_err_over_tol=float((err / tol).max()), max_ulp=float(ulps.max()))
+    report("general9 " + prec, max_err_over_tol=float((err / tol).max()), max_ulp=float(ulps.max()))
     assert np.all(err <= tol)
+    assert np.all(np.diff(lam, axis=1) >= 0)
