@@ -131,8 +131,8 @@ def test_workload3_f32c_angle64_by_disc_ratio(eig3):
     triple angle in binary64 (precision "f32c64") beside the plain one, per bin
     of Delta/J2^3 = 4 sin^2(phi) taken from the oracle's eigenvalues: both stay
     within the compensated tolerance in every bin, and the per-bin maxima (in
-    ulp of max|lambda|) show what binary64 buys where (the measured threshold
-    of the north-star's selective binary64 angle)."""
+    ulp of max|lambda|) show what binary64 buys where, i.e. the threshold below
+    which taking these steps in binary64 would pay."""
     bt = W.workload3(n=200_003, device="cpu", seed=1305)
     A = bt.A.to(dev())
     lam32 = U.to_np(eig3.eigvals(A, precision="f32c"))
