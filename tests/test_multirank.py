@@ -55,3 +55,20 @@ def test_single_process_identity():
     import bench
     assert bench.max_over_ranks(3.5, torch.device("cpu")) == 3.5
     assert bench.rank_seed(1005, 0) == 1005 and bench.rank_seed(1005, 1) != 1005
+
+
+def test_end_to_end_batch_fits_the_shared_host_memory():
+    """Every rank of a node streams its own batch through page-locked host
+    buffers; the batch is halved until all ranks' buffers fit in 70 % of the
+    available host memory (at most 6 halvings)."""
+    from bench import e2e_shift
+    per_rank = 37e9
+    assert e2e_shift(1, per_rank, 206e9) == 0
+    assert e2e_shift(8, per_rank, 206e9) == 2
+    assert e2e_shift(8, per_rank, 900e9) == 0
+    assert e2e_shift(4, per_rank, float("inf")) == 0
+    assert e2e_shift(8, per_rank, 1e6) == 6
+    for world in (1, 2, 4, 8):
+        for avail in (64e9, 206e9, 480e9):
+            k = e2e_shift(world, per_rank, avail)
+            assert k == 6 or world * per_rank / 2 ** k <= 0.7 * avail
