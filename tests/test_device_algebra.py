@@ -1,5 +1,7 @@
-"""The binary64 device source computes the paper's quantities, checked on the
-source text itself with exact (symbolic) arithmetic.
+"""The device source computes the paper's quantities, checked on the source
+text itself with exact (symbolic) arithmetic: the binary64 path
+(csrc/eig3_f64.cuh) and, at the end of this file, the compensated binary32
+invariants (csrc/eig3_f32c.cuh).
 
 The kernels regroup the paper's formulas into shared products and FMAs
 (Algorithms 2, 4 and 5, the trigonometric eigenvalues of Algorithm 6 in
@@ -25,8 +27,10 @@ import pytest
 
 sp = pytest.importorskip("sympy")
 
-SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                   "paper_2511_00292_gb300", "csrc", "eig3_f64.cuh")
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_2511_00292_gb300", "csrc")
+SRC = os.path.join(CSRC, "eig3_f64.cuh")
+SRC_C = os.path.join(CSRC, "eig3_f32c.cuh")
 
 # exact values of the header's constants
 EXACT = {
@@ -47,8 +51,8 @@ class NS:
 # A translator for the C subset of these functions
 # ---------------------------------------------------------------------------
 
-def _source():
-    with open(SRC) as f:
+def _source(path=None):
+    with open(path or SRC) as f:
         return f.read()
 
 
@@ -131,8 +135,12 @@ def _statements(body):
     return out
 
 
-def _expr(e):
-    e = e.replace("{", "[").replace("}", "]")
+def _expr(e, braces="list"):
+    if braces == "pair":  # {hi, lo} initialises a compensated pair
+        e = e.replace("{", "V2(").replace("}", ")")
+    else:
+        e = e.replace("{", "[").replace("}", "]")
+    e = re.sub(r"(\d+\.\d*)f\b", r"\1", e)  # binary32 literals
     e = re.sub(r"dev_scale<\d+>\(\w+\)", "0", e)
     e = re.sub(r"(\w+)<\d+>\(", r"\1(", e)  # sqrt_nonneg<3>( and the like
     e = re.sub(r"(?<![\w.])(\d+\.\d*)", lambda m: f"_Q('{m.group(1)}')", e)
@@ -143,12 +151,13 @@ def _expr(e):
 
 
 TYPES = r"(double|int|bool|float|Adj|Adj3|Inv|Eig|Dx|DxShared)"
+TYPES_C = r"(int|bool|float|F2|Sum|Diag|InvC|Shared|R13)"
 
 
-def _translate(stmt):
+def _translate(stmt, types=TYPES, ctors=None, braces="list"):
     if stmt.startswith("return "):
-        return "__ret__ = " + _expr(stmt[7:])
-    m = re.match(r"^(?:const )?" + TYPES + r"\s+(.*)$", stmt)
+        return "__ret__ = " + _expr(stmt[7:], braces)
+    m = re.match(r"^(?:const )?" + types + r"\s+(.*)$", stmt)
     if m:
         typ, rest = m.groups()
         if typ in ("int", "bool"):  # exponent tests and coalescence flags: set by the caller
@@ -156,30 +165,34 @@ def _translate(stmt):
         lines = []
         for d in _split_top(rest, ","):
             if "=" not in d:
-                lines.append(f"{d.strip()} = NS()")
+                lines.append(f"{d.strip()} = {(ctors or {}).get(typ, 'NS()')}")
                 continue
             lhs, rhs = d.split("=", 1)
-            lines.append(f"{re.sub(r'\[\d+\]', '', lhs.strip())} = {_expr(rhs)}")
+            lines.append(f"{re.sub(r'\[\d+\]', '', lhs.strip())} = {_expr(rhs, braces)}")
         return "\n".join(lines)
     m = re.match(r"^([\w.\[\]]+)\s*=(?!=)\s*(.*)$", stmt)
     if not m:  # a call for its output arguments (the angle): left to the caller
         return ""
-    return f"{m.group(1)} = {_expr(m.group(2))}"
+    return f"{m.group(1)} = {_expr(m.group(2), braces)}"
 
 
-def device_function(name, **fixed):
+def device_function(name, path=None, env=None, types=TYPES, ctors=None, braces="list", **fixed):
     """The device function `name` as a Python callable on sympy values.
     `fixed` binds the names that integer/boolean statements would set."""
-    src = _source()
+    src = _source(path)
     params, body = _definition(src, name)
-    code = "\n".join(_translate(s) for kind, s in _statements(body) if kind == "stmt")
+    # function-like macros of the body become Python functions of the same namespace
+    macros = [f"def {m}({a}): return {_expr(b, braces)}" for m, a, b in
+              re.findall(r"#define (\w+)\(([^)]*)\)\s+(.*)", body)]
+    code = "\n".join(macros + [_translate(s, types, ctors, braces)
+                               for kind, s in _statements(body) if kind == "stmt"])
 
     def fn(*args):
-        env = dict(BASE_ENV)
-        env.update(fixed)
-        env.update(zip(params, args))
-        exec(code, env)
-        return env.get("__ret__")
+        e = dict(BASE_ENV if env is None else env)
+        e.update(fixed)
+        e.update(zip(params, args))
+        exec(code, e)
+        return e.get("__ret__")
 
     fn.code = code
     return fn
@@ -347,3 +360,82 @@ def test_grad_sym_source_is_the_chain_rule():
     for idx in range(6):
         want = aI1 * sp.diff(I1, s[idx]) + b2 * sp.diff(J2, s[idx]) + b3 * sp.diff(J3, s[idx])
         assert zero(G[idx] - want), idx
+
+
+# ---------------------------------------------------------------------------
+# The compensated binary32 source (csrc/eig3_f32c.cuh) in exact arithmetic
+# ---------------------------------------------------------------------------
+#
+# TwoSum and TwoProduct are error-free, so in exact arithmetic every low part
+# is zero and a compensated pair or Sum2 state is its value; the terms the
+# kernels drop (the low-by-low products) vanish with them.  The compensated
+# invariants must then be the definitions exactly (times 6 and 27, at scale 1).
+
+class V:
+    """A compensated pair (h, l) or Sum2 state (s, c), exactly: its value."""
+
+    def __init__(self, v):
+        self.v = sp.sympify(v)
+
+    h = property(lambda self: self.v)
+    s = property(lambda self: self.v)
+    l = property(lambda self: sp.Integer(0))
+    c = property(lambda self: sp.Integer(0))
+
+    def __add__(self, o):
+        return V(self.v + val(o))
+
+    def __sub__(self, o):
+        return V(self.v - val(o))
+
+    def __neg__(self):
+        return V(-self.v)
+
+
+def val(x):
+    return x.v if isinstance(x, V) else x
+
+
+ENV_C = dict(
+    _Q=sp.Rational, NS=NS, V2=lambda a, b: V(val(a) + val(b)),
+    two_sum=lambda a, b: V(val(a) + val(b)), two_prod=lambda a, b: V(val(a) * val(b)),
+    mul=lambda x, y: V(val(x) * val(y)), neg=lambda x: V(-val(x)),
+    scale2=lambda x, p: V(val(x) * val(p)), start=lambda x: V(val(x)),
+    pair=lambda x: V(val(x)), sq=lambda x: V(val(x) ** 2), done=lambda x: V(val(x)),
+    round1=val, __fmul_rn=lambda a, b: val(a) * val(b), __fadd_rn=lambda a, b: val(a) + val(b),
+    __fsub_rn=lambda a, b: val(a) - val(b), __fmaf_rn=lambda a, b, c: val(a) * val(b) + val(c),
+    pow2_from_field=lambda f: 1)
+CTORS_C = {"R13": "NS(r=[None] * 13)"}
+
+
+def f32c_function(name):
+    return device_function(name, path=SRC_C, env=ENV_C, types=TYPES_C, ctors=CTORS_C,
+                           braces="pair", E=127)  # E = 127: the scale 2^(127 - E) is 1
+
+
+ENV_C["diag_parts"] = lambda *a: f32c_function("diag_parts")(*a)
+ENV_C["dx_c"] = lambda *a: f32c_function("dx_c")(*a)
+
+
+def _check_scaled_invariants(o, A):
+    I1, J2, J3 = invariants_of(A)
+    assert o.e == 0
+    assert zero(val(o.I1) - I1)
+    assert zero(val(o.J2x6) - 6 * J2)
+    assert zero(val(o.J3x27) - 27 * J3)
+    assert zero(val(o.D) - (4 * J2 ** 3 - 27 * J3 ** 2))
+
+
+def test_compensated_invariants_sym_source_equals_definitions():
+    """The symmetric compensated invariants (Algorithms 1, 2, 4, 5 with the
+    symmetric identities and reading R1, every r_i summed term by term) are
+    I1, 6 J2, 27 J3 and the discriminant exactly."""
+    s6, A = sym_symbols()
+    _check_scaled_invariants(f32c_function("invariants_sym_c")(*s6), A)
+
+
+def test_compensated_invariants_general_source_equals_definitions():
+    """The general compensated invariants, with dx(A) and dx(A^T) from the
+    same term-by-term dx_c, are I1, 6 J2, 27 J3 and the discriminant exactly."""
+    a, A = general_symbols()
+    _check_scaled_invariants(f32c_function("invariants_general_c")(a), A)
