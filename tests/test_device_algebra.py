@@ -23,6 +23,7 @@ import os
 import re
 from decimal import Decimal, getcontext
 
+import numpy as np
 import pytest
 
 sp = pytest.importorskip("sympy")
@@ -135,23 +136,61 @@ def _statements(body):
     return out
 
 
+def _ternaries(e):
+    """C conditional expressions c ? a : b (nested, parenthesised or not) as
+    Python ((a) if (c) else (b)), outermost first."""
+    while "?" in e:
+        i = e.index("?")
+        start, depth = 0, 0
+        for k in range(i - 1, -1, -1):
+            if e[k] == ")":
+                depth += 1
+            elif e[k] == "(":
+                if depth == 0:
+                    start = k + 1
+                    break
+                depth -= 1
+        end, depth = len(e), 0
+        for k in range(i + 1, len(e)):
+            if e[k] == "(":
+                depth += 1
+            elif e[k] == ")":
+                if depth == 0:
+                    end = k
+                    break
+                depth -= 1
+        grp, q = e[start:end], i - start
+        depth, nested, colon = 0, 0, None
+        for k in range(q + 1, len(grp)):
+            ch = grp[k]
+            depth += ch == "("
+            depth -= ch == ")"
+            if depth == 0 and ch == "?":
+                nested += 1
+            elif depth == 0 and ch == ":":
+                if nested == 0:
+                    colon = k
+                    break
+                nested -= 1
+        cond, a, b = grp[:q], grp[q + 1:colon], grp[colon + 1:]
+        e = e[:start] + f"(({a}) if ({cond}) else ({b}))" + e[end:]
+    return e
+
+
 def _expr(e, braces="list"):
     if braces == "pair":  # {hi, lo} initialises a compensated pair
         e = e.replace("{", "V2(").replace("}", ")")
     else:
         e = e.replace("{", "[").replace("}", "]")
-    e = re.sub(r"(\d+\.\d*)f\b", r"\1", e)  # binary32 literals
+    e = re.sub(r"(\d+\.\d*(?:e[-+]?\d+)?)f\b", r"\1", e)  # binary32 literals
     e = re.sub(r"dev_scale<\d+>\(\w+\)", "0", e)
     e = re.sub(r"(\w+)<\d+>\(", r"\1(", e)  # sqrt_nonneg<3>( and the like
-    e = re.sub(r"(?<![\w.])(\d+\.\d*)", lambda m: f"_Q('{m.group(1)}')", e)
-    t = re.match(r"^\s*(\w+)\s*\?\s*(.+?)\s*:\s*(.+)$", e)
-    if t:
-        e = f"(({t.group(2)}) if {t.group(1)} else ({t.group(3)}))"
-    return e
+    e = re.sub(r"(?<![\w.])(\d+\.\d*(?:e[-+]?\d+)?)", lambda m: f"_Q('{m.group(1)}')", e)
+    return _ternaries(e)
 
 
 TYPES = r"(double|int|bool|float|Adj|Adj3|Inv|Eig|Dx|DxShared)"
-TYPES_C = r"(int|bool|float|F2|Sum|Diag|InvC|Shared|R13)"
+TYPES_C = r"(int|bool|float|F2|Sum|Diag|InvC|Shared|R13|AdjC)"
 
 
 def _translate(stmt, types=TYPES, ctors=None, braces="list"):
@@ -404,13 +443,33 @@ ENV_C = dict(
     pair=lambda x: V(val(x)), sq=lambda x: V(val(x) ** 2), done=lambda x: V(val(x)),
     round1=val, __fmul_rn=lambda a, b: val(a) * val(b), __fadd_rn=lambda a, b: val(a) + val(b),
     __fsub_rn=lambda a, b: val(a) - val(b), __fmaf_rn=lambda a, b, c: val(a) * val(b) + val(c),
-    pow2_from_field=lambda f: 1)
+    fmaf=lambda a, b, c: a * b + c, det2=lambda a, d, b, c: a * d - b * c,
+    pow2_from_field=lambda f: 1, **EXACT)
+# decimal constants of the binary32 source and the exact values they round
+LITERALS_C = {"1.15470053837925152902": "kTwoOverSqrt3",
+              "0.38490017945975050967": "kK",
+              "0.86602540378443864676": "kHalfSqrt3"}
 CTORS_C = {"R13": "NS(r=[None] * 13)"}
 
 
-def f32c_function(name):
-    return device_function(name, path=SRC_C, env=ENV_C, types=TYPES_C, ctors=CTORS_C,
-                           braces="pair", E=127)  # E = 127: the scale 2^(127 - E) is 1
+def f32c_function(name, **fixed):
+    fixed.setdefault("E", 127)  # E = 127: the scale 2^(127 - E) is 1
+    fn = device_function(name, path=SRC_C, env=ENV_C, types=TYPES_C, ctors=CTORS_C,
+                         braces="pair", **fixed)
+    code = fn.code
+    for lit, name_ in LITERALS_C.items():
+        code = code.replace(f"_Q('{lit}')", name_)
+    params, _ = _definition(_source(SRC_C), name)
+
+    def run(*args):
+        e = dict(ENV_C)
+        e.update(fixed)
+        e.update(zip(params, args))
+        exec(code, e)
+        return e.get("__ret__")
+
+    run.code = code
+    return run
 
 
 ENV_C["diag_parts"] = lambda *a: f32c_function("diag_parts")(*a)
@@ -439,3 +498,48 @@ def test_compensated_invariants_general_source_equals_definitions():
     same term-by-term dx_c, are I1, 6 J2, 27 J3 and the discriminant exactly."""
     a, A = general_symbols()
     _check_scaled_invariants(f32c_function("invariants_general_c")(a), A)
+
+
+def test_binary32_constants_are_the_nearest_values():
+    src = _source(SRC_C)
+    for lit, name in LITERALS_C.items():
+        assert lit + "f" in src
+        assert np.float32(float(lit)) == np.float32(float(sp.N(EXACT[name], 30)))
+
+
+def test_compensated_adjoint_scalars_are_root_derivatives():
+    """r a_J2 and r^2 a_J3 of the binary32 adjoint (its divided differences
+    over the gaps (2/sqrt3) r sigma) are the weighted derivatives of the roots
+    of the depressed cubic; checked at exact rational points (the source's
+    range test on r needs a number)."""
+    fn = f32c_function("adjoint_c", z1=False, z2=False)
+    for r, s1, s2, g in ((sp.Rational(3, 2), sp.Rational(1, 5), sp.Rational(2, 3),
+                          (sp.Rational(1, 7), sp.Rational(-2, 3), sp.Rational(5, 4))),
+                         (sp.Rational(7, 100), sp.Rational(1, 1000), sp.Rational(7, 8),
+                          (sp.Integer(2), sp.Integer(-1), sp.Rational(1, 3)))):
+        o = fn(r, s1, s2, *g)
+        _, aJ2, aJ3 = _roots_derivatives(r, s1, s2, g)
+        assert sp.simplify(o.aJ3r2 - r ** 2 * aJ3) == 0
+        assert sp.simplify(o.aJ2r - r * aJ2) == 0
+        assert sp.simplify(o.aI1 - sum(g) / 3) == 0
+        assert o.inv_r == 1 / r
+
+
+@pytest.mark.parametrize("layout", ["general9", "sym6"])
+def test_compensated_gradients_are_the_chain_rule(layout):
+    """The binary32 gradients (dev(A)/r, Kahan 2x2 cofactors, the adjoint's
+    scalars in units of r) are the chain rule through I1, J2, J3."""
+    if layout == "general9":
+        x, A = general_symbols()
+        name, n = "grad_general_c", 9
+    else:
+        x, A = sym_symbols()
+        name, n = "grad_sym_c", 6
+    aI1, b2, b3, ir = sp.symbols("aI1 aJ2r aJ3r2 ir", real=True)
+    G = [None] * n
+    f32c_function(name)(x, NS(aI1=aI1, aJ2r=b2, aJ3r2=b3, inv_r=ir), G)
+    I1, J2, J3 = invariants_of(A)
+    for idx in range(n):
+        want = aI1 * sp.diff(I1, x[idx]) + b2 * ir * sp.diff(J2, x[idx]) + \
+            b3 * ir ** 2 * sp.diff(J3, x[idx])
+        assert zero(val(G[idx]) - want), idx
