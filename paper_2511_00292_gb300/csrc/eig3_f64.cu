@@ -198,37 +198,70 @@ template <int LAYOUT, typename T, bool LAM>
 __global__ void __launch_bounds__(kThreads)
     k_projectors(const T *__restrict__ A, int64_t n, T *__restrict__ lam, T *__restrict__ P) {
   constexpr int N = Width<LAYOUT>::N;
-  __shared__ __align__(16) T sA[2][kTile * N];
-  for_each_row<N, T>(A, n, sA, [&](int64_t i, const T *row) {
-    double a[N];
+  // dynamic shared memory (proj_smem bytes, above the 48 KB of static arrays):
+  // two input tiles, then the tile's outputs, written back coalesced (27 values
+  // per row: a 27-element stride between lanes when stored directly;
+  // conflict-free in shared memory)
+  extern __shared__ __align__(16) unsigned char smem[];
+  T(*sA)[kTile * N] = reinterpret_cast<T(*)[kTile * N]>(smem);
+  T *sP = reinterpret_cast<T *>(smem + sizeof(T) * 2 * kTile * N);
+  T *sL = sP + kTile * 27;
+  for_each_tile<N, 0, T, T>(
+      A, (const T *)nullptr, n, sA, (T(*)[kTile])nullptr,
+      [&](int64_t r0, int rows, const T *tA, const T *) {
+        if ((int)threadIdx.x < rows) {
+          double a[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) a[j] = (double)row[j];
-    const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
-    if constexpr (LAM) {
-      lam[3 * i + 0] = (T)e.l1;
-      lam[3 * i + 1] = (T)e.l2;
-      lam[3 * i + 2] = (T)e.l3;
-    }
-    double E[27];
-    projectors<N>(a, adjoint_units(e.r, e.sigma1, e.sigma2), E);
-    T *q = P + 27 * i;
+          for (int j = 0; j < N; ++j) a[j] = (double)tA[threadIdx.x * N + j];
+          const Eig e = eigvals_from_inv(invariants_of<LAYOUT, N>(a));
+          if constexpr (LAM) {
+            sL[3 * threadIdx.x + 0] = (T)e.l1;
+            sL[3 * threadIdx.x + 1] = (T)e.l2;
+            sL[3 * threadIdx.x + 2] = (T)e.l3;
+          }
+          double E[27];
+          projectors<N>(a, adjoint_units(e.r, e.sigma1, e.sigma2), E);
+          T *q = sP + 27 * threadIdx.x;
 #pragma unroll
-    for (int j = 0; j < 27; ++j) q[j] = (T)E[j];
-  });
+          for (int j = 0; j < 27; ++j) q[j] = (T)E[j];
+        }
+        __syncthreads();  // the tile's outputs are staged; the next barrier protects them
+        tile_store(sP, rows * 27, P, r0 * 27);
+        if constexpr (LAM) tile_store(sL, rows * 3, lam, r0 * 3);
+      });
+}
+
+template <int LAYOUT, typename T, bool LAM>
+constexpr size_t proj_smem() {
+  return sizeof(T) * (2 * kTile * Width<LAYOUT>::N + kTile * 27 + (LAM ? kTile * 3 : 0));
+}
+
+// Launch with the dynamic shared memory the kernel stages through.  The
+// opt-in above 48 KB is a per-device function attribute, set on the first
+// launch on each device (a host call outside any stream, so later launches can
+// be captured into CUDA graphs).
+template <int LAYOUT, typename T, bool LAM>
+cudaError_t proj_launch2(const void *A, int64_t n, void *lam, void *P, cudaStream_t s) {
+  auto k = k_projectors<LAYOUT, T, LAM>;
+  constexpr size_t bytes = proj_smem<LAYOUT, T, LAM>();
+  static bool opted[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !opted[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        (const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) opted[dev] = true;
+  }
+  k<<<grid_for((const void *)k, kThreads, bytes, n), kThreads, bytes, s>>>((const T *)A, n,
+                                                                          (T *)lam, (T *)P);
+  return cudaGetLastError();
 }
 
 template <int LAYOUT, typename T>
 cudaError_t proj_launch(const void *A, int64_t n, void *lam, void *P, cudaStream_t s) {
-  if (lam) {
-    auto k = k_projectors<LAYOUT, T, true>;
-    k<<<grid_for((const void *)k, kThreads, 0, n), kThreads, 0, s>>>((const T *)A, n, (T *)lam,
-                                                                      (T *)P);
-  } else {
-    auto k = k_projectors<LAYOUT, T, false>;
-    k<<<grid_for((const void *)k, kThreads, 0, n), kThreads, 0, s>>>((const T *)A, n, (T *)lam,
-                                                                      (T *)P);
-  }
-  return cudaGetLastError();
+  return lam ? proj_launch2<LAYOUT, T, true>(A, n, lam, P, s)
+             : proj_launch2<LAYOUT, T, false>(A, n, lam, P, s);
 }
 
 template <int LAYOUT, typename T>
