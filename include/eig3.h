@@ -188,6 +188,33 @@ eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int prec
                                   void *stream);
 
 /*
+ * eig3_eigvals_vjp -- the eigenvalues and the gradient of a loss linear in
+ * them, L = sum_k w_k lambda_k, in one pass per matrix: the forward of
+ * eig3_eigvals (Algorithms 1, 2, 4, 5, 6) followed by the vector-Jacobian
+ * product of eig3_eigvals_backward with the weights w, with no adjoint inputs
+ * written or read back.  The gradient is the same quantity,
+ *   grad_A = a_I1 I + a_J2 dev(A)^T + a_J3 dev(cof(dev A))
+ * (Jacobians of J2 and J3: Lemmas of Sections J2 and J3; the chain rule
+ * through Algorithm 6), with the same layout convention for EIG3_SYM6 and the
+ * same cluster-mean rule where two computed eigenvalues coincide exactly; it
+ * is evaluated on the scaled deviatoric data and reuses the products of the
+ * invariants, so it agrees with eig3_eigvals_backward to rounding, not bit
+ * for bit.  The eigenvalues are those of eig3_eigvals bit for bit.  For a
+ * loss that is not linear in lambda use eig3_eigvals + eig3_eigvals_backward
+ * (the weights are then dL/dlambda, which depend on lambda).
+ *   A       device, n matrices (read only).
+ *   w       device, n x 3 of `dtype`: w_k of matrix i at w[3 i + k - 1] (read only).
+ *   lam     device, n x 3 of `dtype` (ascending eigenvalues), or NULL.
+ *   grad_A  device, n x 9 or n x 6 of `dtype`.
+ *   stats   device eig3_stats or NULL (as for eig3_eigvals).
+ * Precisions EIG3_PREC_F64 (EIG3_F64 or EIG3_F32 storage) and
+ * EIG3_PREC_F32_COMP (EIG3_F32); the others return EIG3_ERR_DTYPE.
+ */
+eig3_status eig3_eigvals_vjp(const void *A, int layout, int dtype, int precision, int64_t n,
+                             const void *w, void *lam, void *grad_A, eig3_stats *stats,
+                             void *stream);
+
+/*
  * eig3_eigprojectors -- eigenvalues and eigenprojectors E_1, E_2, E_3.
  * Section 1 of the paper relates the eigenprojectors to the eigenvalue
  * derivatives, E_k^T = d lambda_k / dA; with the Jacobians of J2 and J3

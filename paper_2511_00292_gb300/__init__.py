@@ -18,7 +18,8 @@ from the shifted QR algorithm instead of the closed form; eigenvalues and
 adjoint only).
 
 Entry points: :func:`eigvals`, :func:`eigvals_backward`, :func:`eigvals_ad`
-(autograd), :func:`invariants`, :func:`eigprojectors`, :func:`mohr_coulomb`,
+(autograd), :func:`eigvals_vjp` (eigenvalues and the gradient of a loss linear
+in them, fused), :func:`invariants`, :func:`eigprojectors`, :func:`mohr_coulomb`,
 :func:`eigvals_variant` (the paper's comparison variants), :class:`Stats`;
 host-resident batches stream through :class:`host.HostPipeline`.
 """
@@ -32,7 +33,8 @@ from . import _lib
 from ._lib import (F32, F64, GENERAL9, PREC_F32_COMP, PREC_F64, SYM6, Eig3Error, Eig3Stats,
                    check, load)
 
-__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigprojectors",
+__all__ = ["eigvals", "invariants", "eigvals_backward", "eigvals_ad", "eigvals_vjp",
+           "eigprojectors",
            "mohr_coulomb", "eigvals_variant", "Stats", "Eig3Error", "layout_of", "GENERAL9",
            "SYM6"]
 
@@ -192,6 +194,34 @@ def eigvals_backward(A: torch.Tensor, grad_lam: torch.Tensor, aux=None, layout=N
                                           _stream(dev))
     check(st, "eig3_eigvals_backward")
     return gA
+
+
+def eigvals_vjp(A: torch.Tensor, w: torch.Tensor, layout=None, precision="f64",
+                return_eigvals=True, stats=None, out=None, grad_out=None, device=None):
+    """Eigenvalues (n, 3) and dL/dA for L = sum_k w_k lambda_k in one fused
+    pass (eig3_eigvals_vjp): returns (lam, grad_A), or grad_A alone with
+    ``return_eigvals=False``.  ``w`` is (n, 3) in the storage dtype."""
+    lay = layout_of(A, layout)
+    X = _rows(A, lay)
+    n = X.shape[0]
+    wc = w if w.is_contiguous() else w.contiguous()
+    if wc.dtype != X.dtype or wc.numel() != 3 * n or not (wc.is_cuda or wc.is_pinned()):
+        raise ValueError("w must be a CUDA or pinned (n, 3) tensor of the storage dtype")
+    dev = _device(X, device)
+    lam = None
+    if return_eigvals:
+        lam = _out(out, 3 * n, X.dtype, "out") if out is not None else _alloc((n, 3), X.dtype,
+                                                                             X, dev)
+    gA = (_out(grad_out, X.numel(), X.dtype, "grad_out") if grad_out is not None
+          else _alloc(tuple(X.shape), X.dtype, X, dev))
+    if stats is not None and not (stats.buf.is_cuda and stats.buf.numel() == 6):
+        raise ValueError("stats must be a Stats object")
+    sp = _ptr(stats.buf) if stats is not None else None
+    with torch.cuda.device(dev):
+        st = load().eig3_eigvals_vjp(_ptr(X), lay, _dtype_code(X), _PRECS[precision], n,
+                                     _ptr(wc), _ptr(lam), _ptr(gA), sp, _stream(dev))
+    check(st, "eig3_eigvals_vjp")
+    return (lam, gA) if return_eigvals else gA
 
 
 def eigprojectors(A: torch.Tensor, layout=None, precision="f64", return_eigvals=False,

@@ -12,6 +12,7 @@ EXPORTS = (
     "eig3_invariants",
     "eig3_eigvals",
     "eig3_eigvals_backward",
+    "eig3_eigvals_vjp",
     "eig3_eigprojectors",
     "eig3_mohr_coulomb",
     "eig3_eigvals_variant",
@@ -73,6 +74,8 @@ def load():
         lib.eig3_eigvals.restype = I
         lib.eig3_eigvals_backward.argtypes = [P, I, I, I, I64, P, P, P, P]
         lib.eig3_eigvals_backward.restype = I
+        lib.eig3_eigvals_vjp.argtypes = [P, I, I, I, I64, P, P, P, P, P]
+        lib.eig3_eigvals_vjp.restype = I
         lib.eig3_eigprojectors.argtypes = [P, I, I, I, I64, P, P, P]
         lib.eig3_eigprojectors.restype = I
         lib.eig3_mohr_coulomb.argtypes = [P, I, I, I, I64, ctypes.c_double, ctypes.c_double, P,

@@ -1,6 +1,7 @@
 // eig3_api.cu -- the library's C ABI (include/eig3.h): host-side argument
 // checks, dispatch to the binary64 or compensated binary32 kernels, launch
 // error reporting, and launch-geometry helpers.
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -11,13 +12,17 @@
 namespace eig3 {
 
 int sm_count() {
-  static int cache[64] = {0};
+  // per-device cache; concurrent first calls may both query, then store the same value
+  static std::atomic<int> cache[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-  if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
-  if (dev >= 0 && dev < 64) cache[dev] = v;
+  if (dev >= 0 && dev < 64) cache[dev].store(v, std::memory_order_relaxed);
   return v;
 }
 
@@ -159,6 +164,25 @@ eig3_status eig3_eigvals_backward(const void *A, int layout, int dtype, int prec
   return from_cuda(eig3::launch_backward_f64(A, layout, dtype, n, grad_lam, aux, grad_A, s));
 }
 
+eig3_status eig3_eigvals_vjp(const void *A, int layout, int dtype, int precision, int64_t n,
+                             const void *w, void *lam, void *grad_A, eig3_stats *stats,
+                             void *stream) {
+  eig3_status st = check_modes(layout, dtype, precision, n);
+  if (st != EIG3_OK) return st;
+  if (precision == EIG3_PREC_F64_GUARDED || precision == EIG3_PREC_F32_COMP_A64)
+    return EIG3_ERR_DTYPE;
+  if (n == 0) return EIG3_OK;
+  if (!A || !w || !grad_A) return EIG3_ERR_ARG;
+  const size_t es = elem_size(dtype);
+  if (!aligned(A, es) || !aligned(w, es) || !aligned(grad_A, es) || (lam && !aligned(lam, es)) ||
+      (stats && !aligned(stats, 8)))
+    return EIG3_ERR_ALIGN;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == EIG3_PREC_F32_COMP)
+    return from_cuda(eig3::launch_eigvals_vjp_f32c(A, layout, n, w, lam, grad_A, stats, s));
+  return from_cuda(eig3::launch_eigvals_vjp_f64(A, layout, dtype, n, w, lam, grad_A, stats, s));
+}
+
 eig3_status eig3_eigprojectors(const void *A, int layout, int dtype, int precision, int64_t n,
                                void *lam, void *P, void *stream) {
   eig3_status st = check_modes(layout, dtype, precision, n);
@@ -233,6 +257,6 @@ const char *eig3_status_string(int status) {
   }
 }
 
-int eig3_version(void) { return 10200; }
+int eig3_version(void) { return 10300; }
 
 }  // extern "C"

@@ -1,11 +1,12 @@
 // eig3_f32c.cu -- compensated binary32 kernels (storage and arithmetic in
 // binary32, see eig3_f32c.cuh): invariants, eigenvalues (+ adjoint inputs,
-// + statistics), the adjoint and the eigenprojectors, for both layouts.  One
-// thread per matrix; blocks walk the batch in tiles of 256 rows whose inputs
-// are copied into shared memory asynchronously, one tile ahead (for_each_row /
-// for_each_tile, eig3_tile.cuh); the 16-byte adjoint-input rows move as one
-// float4 each; outputs are stored directly, the projectors through shared
-// memory.
+// + statistics), the adjoint, the fused forward + vector-Jacobian product and
+// the eigenprojectors, for both layouts.  One thread per matrix; the
+// eigenvalue and fused kernels' warps walk the batch in tiles of 32 rows each
+// (for_each_row_warp), the others' blocks in tiles of 256 rows (for_each_row /
+// for_each_tile), the inputs copied into shared memory asynchronously one tile
+// ahead (eig3_tile.cuh); the 16-byte adjoint-input rows move as one float4
+// each; outputs are stored directly, the projectors through shared memory.
 #include <cstdint>
 
 #include "eig3_f32c.cuh"
@@ -37,12 +38,14 @@ struct WidthC {
   static constexpr int N = (LAYOUT == EIG3_GENERAL9) ? 9 : 6;
 };
 
-template <int LAYOUT, int N>
+// EIG: invariants for the eigenvalue kernels (see disc_sym_rounded);
+// otherwise for the invariants output.
+template <int LAYOUT, int N, bool EIG = true>
 __device__ __forceinline__ InvC invariants_c(const float (&a)[N]) {
   if constexpr (LAYOUT == EIG3_GENERAL9) {
     return invariants_general_c(a);
   } else {
-    return invariants_sym_c(a[0], a[1], a[2], a[3], a[4], a[5]);
+    return invariants_sym_c<EIG>(a[0], a[1], a[2], a[3], a[4], a[5]);
   }
 }
 
@@ -54,7 +57,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     float a[N];
     load_f<N>(A, i, a);
-    invariants_out(invariants_c<LAYOUT, N>(a), inv + 4 * i);
+    invariants_out(invariants_c<LAYOUT, N, false>(a), inv + 4 * i);
   }
 }
 
@@ -67,11 +70,11 @@ __global__ void __launch_bounds__(kThreads)
     k_eigvals_c(const float *__restrict__ A, int64_t n, float *__restrict__ lam,
                 float *__restrict__ aux, eig3_stats *__restrict__ stats) {
   constexpr int N = WidthC<LAYOUT>::N;
-  __shared__ __align__(16) float sA[2][kTile * N];
+  __shared__ __align__(16) float sW[kThreads / 32][2][kWarpTile * N];
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
   const bool vaux = AUX && aligned16c(aux);
-  for_each_row<N, float>(A, n, sA, [&](int64_t i, const float *row) {
+  for_each_row_warp<N, float>(A, n, sW[threadIdx.x >> 5], [&](int64_t i, const float *row) {
     float a[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a[j] = row[j];
@@ -145,6 +148,70 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int j = 0; j < N; ++j) q[j] = G[j];
   });
+}
+
+// Fused forward + vector-Jacobian product (eig3_eigvals_vjp): lambda
+// (optional) and dL/dA for L = sum_k w_k lambda_k in one pass per matrix,
+// the adjoint from the forward's r and sigmas in registers.  Rows of A go
+// through the warp's shared-memory tiles; the weights are read directly.
+template <int LAYOUT, bool LAM, bool STATS>
+__global__ void __launch_bounds__(kThreads)
+    k_eigvals_vjp_c(const float *__restrict__ A, const float *__restrict__ w, int64_t n,
+                    float *__restrict__ lam, float *__restrict__ gA,
+                    eig3_stats *__restrict__ stats) {
+  constexpr int N = WidthC<LAYOUT>::N;
+  __shared__ __align__(16) float sW[kThreads / 32][2][kWarpTile * N];
+  StatAcc acc;
+  if constexpr (STATS) stat_init(acc);
+  for_each_row_warp<N, float>(A, n, sW[threadIdx.x >> 5], [&](int64_t i, const float *row) {
+    float a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = row[j];
+    const float g1 = __ldg(w + 3 * i + 0);
+    const float g2 = __ldg(w + 3 * i + 1);
+    const float g3 = __ldg(w + 3 * i + 2);
+    const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+    if constexpr (LAM) {
+      lam[3 * i + 0] = e.l1;
+      lam[3 * i + 1] = e.l2;
+      lam[3 * i + 2] = e.l3;
+    }
+    const AdjC s = adjoint_c(e.r, e.sigma1, e.sigma2, g1, g2, g3);
+    float G[N];
+    if constexpr (LAYOUT == EIG3_GENERAL9) {
+      grad_general_c(a, s, G);
+    } else {
+      grad_sym_c(a, s, G);
+    }
+    float *q = gA + N * i;
+#pragma unroll
+    for (int j = 0; j < N; ++j) q[j] = G[j];
+    if constexpr (STATS) {
+      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0f, fminf(e.sigma1, e.sigma2), e.l1,
+               e.l2, e.l3);
+    }
+  });
+  if constexpr (STATS) stat_flush(acc, stats);
+}
+
+template <int LAYOUT, bool LAM, bool STATS>
+cudaError_t vjp_c4(const void *A, const void *w, int64_t n, void *lam, void *gA, eig3_stats *st,
+                   cudaStream_t s) {
+  auto k = k_eigvals_vjp_c<LAYOUT, LAM, STATS>;
+  const int grid = grid_for((const void *)k, kThreads, 0, n);
+  k<<<grid, kThreads, 0, s>>>((const float *)A, (const float *)w, n, (float *)lam, (float *)gA,
+                              st);
+  return cudaGetLastError();
+}
+
+template <int LAYOUT>
+cudaError_t vjp_c(const void *A, const void *w, int64_t n, void *lam, void *gA, eig3_stats *st,
+                  cudaStream_t s) {
+  if (lam)
+    return st ? vjp_c4<LAYOUT, true, true>(A, w, n, lam, gA, st, s)
+              : vjp_c4<LAYOUT, true, false>(A, w, n, lam, gA, st, s);
+  return st ? vjp_c4<LAYOUT, false, true>(A, w, n, lam, gA, st, s)
+            : vjp_c4<LAYOUT, false, false>(A, w, n, lam, gA, st, s);
 }
 
 template <int LAYOUT, bool LAM>
@@ -261,6 +328,12 @@ cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *l
                                    cudaStream_t s) {
   return layout == EIG3_GENERAL9 ? proj_c<EIG3_GENERAL9>(A, n, lam, P, s)
                                  : proj_c<EIG3_SYM6>(A, n, lam, P, s);
+}
+
+cudaError_t launch_eigvals_vjp_f32c(const void *A, int layout, int64_t n, const void *w, void *lam,
+                                    void *grad_A, eig3_stats *stats, cudaStream_t s) {
+  return layout == EIG3_GENERAL9 ? vjp_c<EIG3_GENERAL9>(A, w, n, lam, grad_A, stats, s)
+                                 : vjp_c<EIG3_SYM6>(A, w, n, lam, grad_A, stats, s);
 }
 
 cudaError_t launch_backward_f32c(const void *A, int layout, int64_t n, const void *grad_lam,

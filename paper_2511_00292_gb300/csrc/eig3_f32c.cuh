@@ -162,6 +162,36 @@ __device__ __forceinline__ Diag diag_parts(float a00, float a11, float a22) {
   return g;
 }
 
+// The discriminant of a symmetric matrix from its r_i (Sum2 states),
+//   Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2,
+// two ways.  disc_sym_compensated keeps it a Sum2 state (the invariants
+// output, accurate at u32^2).  disc_sym_rounded serves the eigenvalue
+// kernels, which round Delta to binary32 before the angle: every term is
+// non-negative, so nothing cancels and no compensation is needed -- each
+// (s + c)^2 is rounded once (sq1) and the terms are summed in a tree, a
+// relative error of a few units of binary32 against the 14 compensated
+// additions of the other form.  The r_i themselves, where the cancellation
+// is, stay compensated either way.
+__device__ __forceinline__ float sq1(Sum r) {
+  return __fmaf_rn(r.s, r.s, __fmul_rn(r.c, __fmaf_rn(2.0f, r.s, r.c)));
+}
+
+__device__ __forceinline__ Sum disc_sym_compensated(Sum r2, Sum r3, Sum r4, Sum r8, Sum r9,
+                                                    Sum r10, Sum r11, Sum r12, Sum r13,
+                                                    Sum r14) {
+  const Sum g14 = start(sq(r2)) + sq(r3) + sq(r4);
+  const Sum g2 = start(sq(r8)) + sq(r9) + sq(r10) + sq(r11) + sq(r12) + sq(r13);
+  return start(mul(pair(g14), 14.0f)) + scale2(pair(g2), 2.0f) + sq(r14);
+}
+
+__device__ __forceinline__ Sum disc_sym_rounded(Sum r2, Sum r3, Sum r4, Sum r8, Sum r9, Sum r10,
+                                                Sum r11, Sum r12, Sum r13, Sum r14) {
+  const float g14 = __fadd_rn(__fadd_rn(sq1(r2), sq1(r3)), sq1(r4));
+  const float g2 = __fadd_rn(__fadd_rn(__fadd_rn(sq1(r8), sq1(r9)), __fadd_rn(sq1(r10), sq1(r11))),
+                             __fadd_rn(sq1(r12), sq1(r13)));
+  return {__fmaf_rn(14.0f, g14, __fmaf_rn(2.0f, g2, sq1(r14))), 0.0f};
+}
+
 // ---------------------------------------------------------------------------
 // Symmetric matrix (A00, A11, A22, A12, A02, A01) with a = A01, b = A02,
 // c = A12.  The r_i of Algorithm 5 are summed term by term as the paper
@@ -178,6 +208,9 @@ __device__ __forceinline__ Diag diag_parts(float a00, float a11, float a22) {
 //   r14 = d0d1d2 - aa d0 + bb d1 - cc d2
 //   Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2.
 // ---------------------------------------------------------------------------
+// EIG: for the eigenvalue kernels (Delta by disc_sym_rounded); otherwise the
+// invariants output (disc_sym_compensated).
+template <bool EIG = false>
 __device__ __forceinline__ InvC invariants_sym_c(float a00, float a11, float a22, float c0,
                                                  float b0, float a0) {
   const Diag g = diag_parts(a00, a11, a22);
@@ -217,9 +250,8 @@ __device__ __forceinline__ InvC invariants_sym_c(float a00, float a11, float a22
   const Sum r13 = s1213 + mul(ac, d2) - aab;
   const Sum r12 = -s1213 + mul(ac, d0) + ccb;
   const Sum r14 = start(mul(d0d1, d2)) - mul(aa, d0) + mul(bb, d1) - mul(cc, d2);
-  const Sum g14 = start(sq(r2)) + sq(r3) + sq(r4);
-  const Sum g2 = start(sq(r8)) + sq(r9) + sq(r10) + sq(r11) + sq(r12) + sq(r13);
-  o.D = start(mul(pair(g14), 14.0f)) + scale2(pair(g2), 2.0f) + sq(r14);
+  o.D = EIG ? disc_sym_rounded(r2, r3, r4, r8, r9, r10, r11, r12, r13, r14)
+            : disc_sym_compensated(r2, r3, r4, r8, r9, r10, r11, r12, r13, r14);
   return o;
 }
 
@@ -389,7 +421,11 @@ __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
   }
   o.I1 = round1(v.I1);
   const float k = o.r * 0.38490017945975050967f;
-  const float i3 = __fdiv_rn(o.I1, 3.0f);
+  // I1 / 3 correctly rounded: the product with the binary32 reciprocal of 3
+  // and one FMA correction (q0 + (I1 - 3 q0)/3; exhaustively checked over a
+  // binade, so for every normal I1), instead of an IEEE division
+  const float q0 = __fmul_rn(o.I1, 0.333333343267f);
+  const float i3 = __fmaf_rn(__fmaf_rn(-3.0f, q0, o.I1), 0.333333343267f, q0);
   o.l1 = fmaf(-k, fmaf(2.0f, o.sigma1, o.sigma2), i3);
   o.l2 = fmaf(k, o.sigma1 - o.sigma2, i3);
   o.l3 = fmaf(k, fmaf(2.0f, o.sigma2, o.sigma1), i3);

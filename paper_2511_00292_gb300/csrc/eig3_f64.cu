@@ -2,13 +2,16 @@
 // + statistics) and the adjoint, for the general 9-entry and symmetric
 // 6-entry layouts with binary64 or binary32 storage.
 //
-// One thread per matrix.  Blocks of 256 threads walk the batch in tiles of 256
-// rows (grid-stride over tiles, grid sized to fill every SM).  The input rows
-// of the next tile are copied into shared memory with asynchronous 16-byte
-// copies while the current tile is computed (for_each_row / for_each_tile,
-// eig3_tile.cuh); the adjoint inputs (16- or 32-byte rows) move with direct
-// vector accesses and the outputs are stored directly.  The binary64 path is bound by the FP64 pipe
+// One thread per matrix.  The eigenvalue kernel's warps walk the batch in
+// tiles of 32 rows each (for_each_row_warp: no block barrier); the other
+// kernels' blocks of 256 threads in tiles of 256 rows (for_each_row /
+// for_each_tile); either way the grid is sized to fill every SM and the input
+// rows of the next tile are copied into shared memory with asynchronous
+// 16-byte copies while the current tile is computed (eig3_tile.cuh).  The
+// adjoint inputs (16- or 32-byte rows) move with direct vector accesses and
+// the outputs are stored directly.  The binary64 path is bound by the FP64 pipe
 // (two DFMA per SM per clock on GB300, far below what HBM could feed).
+#include <atomic>
 #include <cstdint>
 
 #include "eig3_f64.cuh"
@@ -129,11 +132,11 @@ __global__ void __launch_bounds__(kThreads)
     k_eigvals(const T *__restrict__ A, int64_t n, T *__restrict__ lam, T *__restrict__ aux,
               eig3_stats *__restrict__ stats) {
   constexpr int N = Width<LAYOUT>::N;
-  __shared__ __align__(16) T sA[2][kTile * N];
+  __shared__ __align__(16) T sW[kThreads / 32][2][kWarpTile * N];
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
   const bool vaux = AUX && aligned16(aux);
-  for_each_row<N, T>(A, n, sA, [&](int64_t i, const T *row) {
+  for_each_row_warp<N, T>(A, n, sW[threadIdx.x >> 5], [&](int64_t i, const T *row) {
     double a[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a[j] = (double)row[j];
@@ -147,8 +150,57 @@ __global__ void __launch_bounds__(kThreads)
       store_aux<T>(aux, i, vaux, x);
     }
     if constexpr (STATS) {
-      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
+      stat_add(acc, e.d_clamped, e.j2_clamped, __double_as_longlong(e.r) > 0,
                seed_float(min_nonneg(e.sigma1, e.sigma2)), (T)e.l1, (T)e.l2, (T)e.l3);
+    }
+  });
+  if constexpr (STATS) stat_flush(acc, stats);
+}
+
+// Fused forward + vector-Jacobian product: lambda (optional) and
+// dL/dA for L = sum_k w_k lambda_k, one pass per matrix (eig3_eigvals_vjp).
+// The rows of A go through the warp's shared-memory tiles; the three weights
+// of a row are read directly (24 or 12 bytes, contiguous across the warp).
+template <int LAYOUT, typename T, bool LAM, bool STATS>
+__global__ void __launch_bounds__(kThreads)
+    k_eigvals_vjp(const T *__restrict__ A, const T *__restrict__ w, int64_t n,
+                  T *__restrict__ lam, T *__restrict__ gA, eig3_stats *__restrict__ stats) {
+  constexpr int N = Width<LAYOUT>::N;
+  __shared__ __align__(16) T sW[kThreads / 32][2][kWarpTile * N];
+  StatAcc acc;
+  if constexpr (STATS) stat_init(acc);
+  for_each_row_warp<N, T>(A, n, sW[threadIdx.x >> 5], [&](int64_t i, const T *row) {
+    double a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = (double)row[j];
+    const double g1 = (double)__ldg(w + 3 * i + 0);
+    const double g2 = (double)__ldg(w + 3 * i + 1);
+    const double g3 = (double)__ldg(w + 3 * i + 2);
+    double G[N];
+    EigV f;
+    if constexpr (LAYOUT == EIG3_GENERAL9) {
+      ShareG x;
+      const Inv v = invariants_general(a, &x);
+      f = eigvals_vjp_fwd(v);
+      grad_general_vjp(x, v.J2, adjoint_vjp(f, g1, g2, g3), G);
+    } else {
+      ShareS x;
+      const Inv v = invariants_sym(a, &x);
+      f = eigvals_vjp_fwd(v);
+      grad_sym_vjp(x, v.J2, adjoint_vjp(f, g1, g2, g3), G);
+    }
+    if constexpr (LAM) {
+      lam[3 * i + 0] = (T)f.e.l1;
+      lam[3 * i + 1] = (T)f.e.l2;
+      lam[3 * i + 2] = (T)f.e.l3;
+    }
+    T *q = gA + N * i;
+#pragma unroll
+    for (int j = 0; j < N; ++j) q[j] = (T)G[j];
+    if constexpr (STATS) {
+      stat_add(acc, f.e.d_clamped, f.e.j2_clamped, __double_as_longlong(f.m) > 0,
+               seed_float(min_nonneg(f.e.sigma1, f.e.sigma2)), (T)f.e.l1, (T)f.e.l2,
+               (T)f.e.l3);
     }
   });
   if constexpr (STATS) stat_flush(acc, stats);
@@ -244,14 +296,16 @@ template <int LAYOUT, typename T, bool LAM>
 cudaError_t proj_launch2(const void *A, int64_t n, void *lam, void *P, cudaStream_t s) {
   auto k = k_projectors<LAYOUT, T, LAM>;
   constexpr size_t bytes = proj_smem<LAYOUT, T, LAM>();
-  static bool opted[64] = {false};
+  // one flag per device; host threads may race to set it, which only repeats
+  // the (idempotent) attribute call
+  static std::atomic<bool> opted[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !opted[dev]) {
+  if (dev < 0 || dev >= 64 || !opted[dev].load(std::memory_order_acquire)) {
     const cudaError_t e = cudaFuncSetAttribute(
         (const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) opted[dev] = true;
+    if (dev >= 0 && dev < 64) opted[dev].store(true, std::memory_order_release);
   }
   k<<<grid_for((const void *)k, kThreads, bytes, n), kThreads, bytes, s>>>((const T *)A, n,
                                                                           (T *)lam, (T *)P);
@@ -290,6 +344,26 @@ cudaError_t eig_launch(const void *A, int64_t n, void *lam, void *aux, eig3_stat
   }
   return st ? eig_launch4<LAYOUT, T, false, true>(A, n, lam, aux, st, s)
             : eig_launch4<LAYOUT, T, false, false>(A, n, lam, aux, st, s);
+}
+
+template <int LAYOUT, typename T, bool LAM, bool STATS>
+cudaError_t vjp_launch4(const void *A, const void *w, int64_t n, void *lam, void *gA,
+                        eig3_stats *st, cudaStream_t s) {
+  auto k = k_eigvals_vjp<LAYOUT, T, LAM, STATS>;
+  const int grid = grid_for((const void *)k, kThreads, 0, n);
+  k<<<grid, kThreads, 0, s>>>((const T *)A, (const T *)w, n, (T *)lam, (T *)gA, st);
+  return cudaGetLastError();
+}
+
+template <int LAYOUT, typename T>
+cudaError_t vjp_launch(const void *A, const void *w, int64_t n, void *lam, void *gA,
+                       eig3_stats *st, cudaStream_t s) {
+  if (lam) {
+    return st ? vjp_launch4<LAYOUT, T, true, true>(A, w, n, lam, gA, st, s)
+              : vjp_launch4<LAYOUT, T, true, false>(A, w, n, lam, gA, st, s);
+  }
+  return st ? vjp_launch4<LAYOUT, T, false, true>(A, w, n, lam, gA, st, s)
+            : vjp_launch4<LAYOUT, T, false, false>(A, w, n, lam, gA, st, s);
 }
 
 template <int LAYOUT, typename T, bool AUX>
@@ -335,6 +409,16 @@ cudaError_t launch_projectors_f64(const void *A, int layout, int dtype, int64_t 
                              : proj_launch<EIG3_GENERAL9, float>(A, n, lam, P, s);
   return dtype == EIG3_F64 ? proj_launch<EIG3_SYM6, double>(A, n, lam, P, s)
                            : proj_launch<EIG3_SYM6, float>(A, n, lam, P, s);
+}
+
+cudaError_t launch_eigvals_vjp_f64(const void *A, int layout, int dtype, int64_t n, const void *w,
+                                   void *lam, void *grad_A, eig3_stats *stats, cudaStream_t s) {
+  if (layout == EIG3_GENERAL9)
+    return dtype == EIG3_F64
+               ? vjp_launch<EIG3_GENERAL9, double>(A, w, n, lam, grad_A, stats, s)
+               : vjp_launch<EIG3_GENERAL9, float>(A, w, n, lam, grad_A, stats, s);
+  return dtype == EIG3_F64 ? vjp_launch<EIG3_SYM6, double>(A, w, n, lam, grad_A, stats, s)
+                           : vjp_launch<EIG3_SYM6, float>(A, w, n, lam, grad_A, stats, s);
 }
 
 cudaError_t launch_backward_f64(const void *A, int layout, int dtype, int64_t n,

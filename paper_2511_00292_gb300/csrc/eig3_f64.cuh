@@ -115,20 +115,33 @@ __device__ __forceinline__ double widen_scaled(float f, int s) {
 // truncated after t^2 (the next term is below 2^-60 g).  Forming t from the
 // rounded g cancels half of g's rounding error.  Zero and subnormal x give 0;
 // infinity and NaN pass through.
+//
+// sqrt_nonneg_split returns the same root as a product sqrt(C x) = s 2^k with
+// s = sqrt(C x') in [1, 2 sqrt3) (k set; s = 0, k = 0 for zero and subnormal
+// x; s = x, k = 0 for infinity and NaN), for callers that want the scale of
+// the root apart from it.
 template <int C = 1>
-__device__ __forceinline__ double sqrt_nonneg(double x) {
+__device__ __forceinline__ double sqrt_nonneg_split(double x, int &k) {
   static_assert(C == 1 || C == 3, "factor 1 or 3");
   const int hi = __double2hiint(x);
   const int E = (hi >> 20) & 0x7ff;
-  const int k = (E - 1023) >> 1;
-  const double xs = __hiloint2double(hi - (k << 21), __double2loint(x));
+  const int kk = (E - 1023) >> 1;
+  const double xs = __hiloint2double(hi - (kk << 21), __double2loint(x));
   float y0 = rsqrt_seed((float)C * seed_float(xs));
   if (C == 3) y0 = __int_as_float(__float_as_int(y0) & ~3);
   const double g = xs * widen((float)C * y0);
   const double h = fma(-g, widen(0.5f * y0), 0.5);  // t / 2
   const double s = fma(g * h, fma(1.5, h, 1.0), g);
-  const double r = __hiloint2double(__double2hiint(s) + (k << 20), __double2loint(s));
-  return (E == 0) ? 0.0 : ((E == 0x7ff) ? x : r);
+  const bool special = (E == 0) || (E == 0x7ff);
+  k = special ? 0 : kk;
+  return (E == 0) ? 0.0 : ((E == 0x7ff) ? x : s);
+}
+
+template <int C = 1>
+__device__ __forceinline__ double sqrt_nonneg(double x) {
+  int k;
+  const double s = sqrt_nonneg_split<C>(x, k);
+  return __hiloint2double(__double2hiint(s) + (k << 20), __double2loint(s));
 }
 
 // 1/x for positive normal x: with x = 2^k x', x' in [1, 2), the binary32
@@ -142,6 +155,57 @@ __device__ __forceinline__ double recip_pos(double x) {
   const double e = fma(-xs, c0, 1.0);
   const double c = fma(c0, fma(e, e, e), c0);
   return __hiloint2double(__double2hiint(c) - (k << 20), __double2loint(c));
+}
+
+// x 2^k by adding k to the exponent field (integer pipe): exact for normal x
+// whose result stays below the overflow threshold, which the caller ensures
+// (|k| small, |x| far from it).  Zero, subnormal and non-finite x are
+// returned unchanged, so zeros stay exact; a subnormal x enters its
+// product without the factor, an error below 2^-1019 |y| for x y that the
+// callers' magnitudes (deviatoric data scaled into [2^-150, 2^150]) keep far
+// under every rounding error of the sums it enters.
+// Written in PTX: from the same steps in C the compiler may recognise a
+// multiplication by 2^k and issue it on the FP64 pipe.
+__device__ __forceinline__ double times_pow2(double x, int k) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi, f, t;\n\t.reg .pred p, q;\n\t"
+      "mov.b64 {lo, hi}, %1;\n\tand.b32 f, hi, 0x7ff00000;\n\t"
+      "setp.ne.u32 p, f, 0;\n\tsetp.ne.u32 q, f, 0x7ff00000;\n\tand.pred p, p, q;\n\t"
+      "add.s32 t, hi, %2;\n\tselp.b32 hi, t, hi, p;\n\tmov.b64 %0, {lo, hi};\n\t}"
+      : "=d"(r)
+      : "d"(x), "r"(k << 20));
+  return r;
+}
+
+// x 2^k for any x and |k| < 2^11 by exponent arithmetic, saturating: a
+// result beyond the binary64 range becomes +-infinity, one below the normal
+// range +-0 (no subnormal results); zero, subnormal and non-finite x are
+// returned unchanged.  For rarely taken rescalings that must not touch the
+// FP64 pipe.
+__device__ __forceinline__ double times_pow2_sat(double x, int k) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi, e, ne, sg, t, l2;\n\t.reg .pred pk, po, pu;\n\t"
+      "mov.b64 {lo, hi}, %1;\n\tbfe.u32 e, hi, 20, 11;\n\tadd.s32 ne, e, %2;\n\t"
+      "and.b32 sg, hi, 0x80000000;\n\tsetp.ne.u32 pk, e, 0;\n\t"
+      "setp.ne.and.u32 pk, e, 2047, pk;\n\tsetp.ge.s32 po, ne, 2047;\n\t"
+      "setp.le.s32 pu, ne, 0;\n\tshl.b32 t, %2, 20;\n\tadd.s32 t, hi, t;\n\t"
+      "mov.b32 l2, lo;\n\t@po or.b32 t, sg, 0x7ff00000;\n\t@po mov.b32 l2, 0;\n\t"
+      "@pu mov.b32 t, sg;\n\t@pu mov.b32 l2, 0;\n\tselp.b32 hi, t, hi, pk;\n\t"
+      "selp.b32 lo, l2, lo, pk;\n\tmov.b64 %0, {lo, hi};\n\t}"
+      : "=d"(r)
+      : "d"(x), "r"(k));
+  return r;
+}
+
+// |x| by clearing the sign bit (integer pipe, in PTX for the same reason: a
+// floating-point absolute value would take an FP64-pipe slot).
+__device__ __forceinline__ double abs_bits64(double x) {
+  double r;
+  asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tand.b32 hi, hi, 0x7fffffff;\n\t"
+      "mov.b64 %0, {lo, hi};\n\t}"
+      : "=d"(r)
+      : "d"(x));
+  return r;
 }
 
 // min of two non-negative doubles: their bit patterns order like their values.
@@ -170,6 +234,25 @@ __device__ __forceinline__ int dev_scale(double (&v)[N]) {
   }
   return e;
 }
+
+// What the invariants hand on to the fused vector-Jacobian product, all of
+// the scaled data 2^-e A: the sums that give dev(A)'s diagonal,
+// 3 (S00, S11, S22) = (tn, -t2, -t1), the off-diagonal entries, and the pair
+// products that the cofactors of S = dev(A) are made of.  Filled only when
+// the caller asks for it (a null pointer otherwise; nothing is then kept).
+struct ShareG {
+  double t1, t2, tn;
+  double a01, a02, a10, a12, a20, a21;
+  double p01, p02, p12;                              // A01 A10, A02 A20, A12 A21
+  double m0112, m0210, m0221, m2001, m1021, m2012;   // A01 A12, A02 A10, A02 A21,
+                                                     // A20 A01, A10 A21, A20 A12
+};
+
+struct ShareS {
+  double t1, t2, tn;
+  double a, b, c;                 // A01, A02, A12
+  double aa, bb, cc, ab, ac, bc;  // their products
+};
 
 // --------------------------------------------------------------------------
 // General 9-entry matrix: Algorithms 1, 2, 4, 5.
@@ -204,6 +287,7 @@ struct DxShared {
 
 struct Dx {
   double r2, r3, r4, r5, r6, r7, r8, r9, r10, r11, r12, r13;  // r1 is formed by the caller
+  double m0221;                                               // M02 M21
 };
 
 // r2 .. r13 of dx(M); m0112 = M01 M12 and m0210 = M02 M10 come from the caller
@@ -227,11 +311,13 @@ __device__ __forceinline__ Dx dx13(double M01, double M02, double M10, double M1
   r.r11 = fma(M01, s.q11, s.d1 * m0221);
   r.r12 = fma(M02, s.q12, s.d0 * m0112);
   r.r13 = fma(M02, s.q13, s.d2 * m0112);
+  r.m0221 = m0221;
   return r;
 }
 
-// a[0..8] row-major.  Returns the four invariants (unclamped).
-__device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
+// a[0..8] row-major.  Returns the four invariants (unclamped); fills *x when
+// given (see ShareG).
+__device__ __forceinline__ Inv invariants_general(const double (&a)[9], ShareG *x = nullptr) {
   const double a00 = a[0], a11 = a[4], a22 = a[8];
   Inv o;
   // Algorithm 1
@@ -249,23 +335,26 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
   s.p12 = a12 * a21;
   // Algorithm 2: diag/6 + offdiag
   o.J2 = fma(fma(s.d0, s.d0, fma(s.d1, s.d1, s.d2 * s.d2)), kInv6, (s.p01 + s.p02) + s.p12);
-  // Algorithm 4: offdiag + mixed/3 - t1 t2 t3 / 27, with mixed/3 - t1 t2 t3/27
-  // grouped as (1/3) [t1 (A01 A10 - t2 t3 / 9) + A02 A20 t2 + A12 A21 t3]
+  // Algorithm 5's differences of the paired products, shared with J3:
+  // e8 = A01 A10 - A12 A21, e9 = A02 A20 - A12 A21
+  s.e8 = s.p01 - s.p12;
+  s.e9 = s.p02 - s.p12;
+  // Algorithm 4: offdiag + mixed/3 - t1 t2 t3 / 27 with t1 = d1 + d2,
+  // t2 = d0 - d2, t3 = -(d0 + d1) = -tn.  As t1 + t2 + t3 = 0,
+  // mixed = A01 A10 t1 + A02 A20 t2 + A12 A21 t3 = t1 e8 + t2 e9, so
+  //   mixed/3 - t1 t2 t3/27 = (1/3) [t1 (e8 + t2 tn / 9) + t2 e9]
   const double t1 = s.d1 + s.d2;
   const double t2 = s.d0 - s.d2;
-  const double t3 = -s.d0 - s.d1;
+  const double tn = s.d0 + s.d1;
   // A01 A12 A20 + A02 A10 A21; the same two triple products give r1 of
   // Algorithm 5 for A, and r1 for A^T is its negative (A10 A21 A02 - A20 A01 A12)
   const double m0112 = a01 * a12, m0210 = a02 * a10;
   const double q = m0210 * a21;
   const double offdiag = fma(m0112, a20, q);
-  const double u01 = fma(-t2, t3 * kInv9, s.p01);
-  o.J3 = fma(fma(t1, u01, fma(s.p02, t2, s.p12 * t3)), kInv3, offdiag);
+  o.J3 = fma(fma(t1, fma(t2, tn * kInv9, s.e8), t2 * s.e9), kInv3, offdiag);
   // Algorithm 5 (reading R1 for r10).  The bracketed sums of r10 .. r14 are
   // single FMAs (d1 d2 + (A02 A20 - A01 A10) and so on); p12 - p01 = -e8 and
   // p12 - p02 = -e9 exactly.
-  s.e8 = s.p01 - s.p12;
-  s.e9 = s.p02 - s.p12;
   const double f0201 = s.p02 - s.p01;
   s.q10 = fma(s.d1, s.d2, f0201);
   s.q11 = fma(s.d1, s.d2, -s.e8);
@@ -273,16 +362,27 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
   s.q13 = fma(s.d0, s.d2, f0201);
   const double r14 = fma(s.d0, fma(s.d1, s.d2, -s.p01), fma(s.d1, s.p02, -(s.d2 * s.p12)));
   const double r1 = fma(m0112, a20, -q);
+  const double m1021 = a10 * a21, m2001 = a20 * a01;
   const Dx u = dx13(a01, a02, a10, a12, a20, a21, m0112, m0210, s);
-  const Dx v = dx13(a10, a20, a01, a21, a02, a12, a10 * a21, a20 * a01, s);
-  // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1), grouped by weight
-  const double g6 = fma(u.r2, v.r2, fma(u.r3, v.r3, u.r4 * v.r4));
-  const double g8 = fma(u.r5, v.r5, fma(u.r6, v.r6, u.r7 * v.r7));
-  const double g2 = fma(u.r8, v.r8,
-                        fma(u.r9, v.r9,
-                            fma(u.r10, v.r10, fma(u.r11, v.r11, fma(u.r12, v.r12, u.r13 * v.r13)))));
-  // w1 u1 v1 = 9 r1 (-r1)
-  o.D = fma(-9.0 * r1, r1, fma(6.0, g6, fma(8.0, g8, fma(2.0, g2, r14 * r14))));
+  const Dx v = dx13(a10, a20, a01, a21, a02, a12, m1021, m2001, s);
+  if (x) {
+    *x = ShareG{t1,    t2,    tn,    a01,   a02,     a10,   a12,  a20,     a21,
+                s.p01, s.p02, s.p12, m0112, m0210, u.m0221, m2001, m1021, v.m0221};
+  }
+  // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1), as one FMA
+  // chain: w1 u1 v1 = 9 r1 (-r1), the power-of-two weights 2 and 8 applied to
+  // u_i exactly on the integer pipe (times_pow2), the weight-6 group last
+  double acc = fma(-9.0 * r1, r1, r14 * r14);
+  acc = fma(times_pow2(u.r13, 1), v.r13, acc);
+  acc = fma(times_pow2(u.r12, 1), v.r12, acc);
+  acc = fma(times_pow2(u.r11, 1), v.r11, acc);
+  acc = fma(times_pow2(u.r10, 1), v.r10, acc);
+  acc = fma(times_pow2(u.r9, 1), v.r9, acc);
+  acc = fma(times_pow2(u.r8, 1), v.r8, acc);
+  acc = fma(times_pow2(u.r7, 3), v.r7, acc);
+  acc = fma(times_pow2(u.r6, 3), v.r6, acc);
+  acc = fma(times_pow2(u.r5, 3), v.r5, acc);
+  o.D = fma(6.0, fma(u.r2, v.r2, fma(u.r3, v.r3, u.r4 * v.r4)), acc);
   return o;
 }
 
@@ -291,7 +391,7 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9]) {
 // With A = A^T, dx(A) = dx(A^T), r1 = 0, r2 = r7, r3 = r5, r4 = r6, so
 // Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
+__device__ __forceinline__ Inv invariants_sym(const double (&s6)[6], ShareS *x = nullptr) {
   const double a00 = s6[0], a11 = s6[1], a22 = s6[2];
   Inv o;
   o.I1 = (a00 + a11) + a22;
@@ -304,11 +404,13 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
   const double aa = a * a, bb = b * b, cc = c * c;
   const double ab = a * b, ac = a * c, bc = b * c;
   o.J2 = fma(fma(d0, d0, fma(d1, d1, d2 * d2)), kInv6, (aa + bb) + cc);
-  const double t1 = d1 + d2, t2 = d0 - d2, t3 = -d0 - d1;
-  const double offdiag = 2.0 * (ab * c);
-  const double uaa = fma(-t2, t3 * kInv9, aa);
-  o.J3 = fma(fma(t1, uaa, fma(bb, t2, cc * t3)), kInv3, offdiag);
+  // Algorithm 4 as in the general case, (1/3) [t1 (e8 + t2 tn / 9) + t2 e9]
+  // with e8 = aa - cc, e9 = bb - cc
   const double fba = bb - aa, fac = aa - cc, fbc = bb - cc;
+  const double t1 = d1 + d2, t2 = d0 - d2, tn = d0 + d1;
+  const double offdiag = 2.0 * (ab * c);
+  o.J3 = fma(fma(t1, fma(t2, tn * kInv9, fac), t2 * fbc), kInv3, offdiag);
+  if (x) *x = ShareS{t1, t2, tn, a, b, c, aa, bb, cc, ab, ac, bc};
   const double r2 = fma(a, fma(-b, d2, ac), -(b * bc));
   const double r3 = fma(a, fma(c, d1, -ab), c * bc);
   const double r4 = fma(c, fma(b, d0, ac), -(b * ab));
@@ -319,10 +421,16 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
   const double r12 = fma(b, fma(-d0, d2, -fbc), d0 * ac);
   const double r13 = fma(b, fma(d0, d2, fba), d2 * ac);
   const double r14 = fma(d0, fma(d1, d2, -aa), fma(d1, bb, -(d2 * cc)));
-  const double g14 = fma(r2, r2, fma(r3, r3, r4 * r4));
-  const double g2 =
-      fma(r8, r8, fma(r9, r9, fma(r10, r10, fma(r11, r11, fma(r12, r12, r13 * r13)))));
-  o.D = fma(14.0, g14, fma(2.0, g2, r14 * r14));
+  // 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2 as one FMA chain, the
+  // weight 2 applied on the integer pipe (times_pow2)
+  double acc = r14 * r14;
+  acc = fma(times_pow2(r13, 1), r13, acc);
+  acc = fma(times_pow2(r12, 1), r12, acc);
+  acc = fma(times_pow2(r11, 1), r11, acc);
+  acc = fma(times_pow2(r10, 1), r10, acc);
+  acc = fma(times_pow2(r9, 1), r9, acc);
+  acc = fma(times_pow2(r8, 1), r8, acc);
+  o.D = fma(14.0, fma(r2, r2, fma(r3, r3, r4 * r4)), acc);
   return o;
 }
 
@@ -350,7 +458,7 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6]) {
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void triple_angle_sines(double x, double y, double &sigma1,
                                                    double &sigma2) {
-  const double ax = fabs(x);
+  const double ax = abs_bits64(x);
   // the seeds are taken from 2^-s |x| and 2^-s y, s the exponent of max(|x|, y),
   // so that their maximum lies in [1, 2); the binary64 steps below use |x| and y
   // themselves (|z| < 2^460 for the scaled deviatoric data)
@@ -662,6 +770,184 @@ __device__ __forceinline__ void grad_sym(const double (&s6)[6], const Adj &s, do
   G[3] = fma(b2x2, S12, b3x2 * C12);
   G[4] = fma(b2x2, S02, b3x2 * C02);
   G[5] = fma(b2x2, S01, b3x2 * C01);
+}
+
+// --------------------------------------------------------------------------
+// Fused forward + vector-Jacobian product (eig3_eigvals_vjp): the eigenvalues
+// and the gradient of L = sum_k w_k lambda_k in one pass per matrix.  The
+// adjoint is taken in the frame of the scaled data 2^-e A: the part
+// a_J2 dev(A)^T + a_J3 dev(cof dev A) of the gradient is homogeneous of degree
+// 0 in dev(A), and the scaling is by a power of two, so the scaled data give
+// it exactly; and the quantities the invariants formed are reused:
+//   * dev(A)'s diagonal from the sums t1, t2, tn of Algorithm 4,
+//     3 (S00, S11, S22) = (tn, -t2, -t1);
+//   * every cofactor of S = dev(A) is one FMA on a pair product of Algorithms
+//     2, 4 and 5: C00 = S11 S22 - A12 A21, C01 = A12 A20 - S10 S22, and so on;
+//   * tr(cof S) = ((tr S)^2 - tr(S^2)) / 2 = -J2 for the trace-free S, so the
+//     diagonal shift of dev(cof S) is the computed J2 / 3;
+//   * r = m 2^kr from the square root's own split, and kK m serves both the
+//     eigenvalue offsets and the adjoint.
+// --------------------------------------------------------------------------
+struct EigV {
+  Eig e;       // eigenvalues of A (l1, l2, l3), the sigmas and the clamp flags
+  double m;    // r of 2^-e A = m 2^kr, m in [1, 2 sqrt3); 0 for r = 0
+  int kr;
+  double kKm;  // kK m
+  double c12;  // 2 sigma1 + sigma2
+};
+
+// Algorithm 6 as in eigvals_from_inv (the same eigenvalues bit for bit), with
+// the scale of r kept apart.
+__device__ __forceinline__ EigV eigvals_vjp_fwd(const Inv &v) {
+  EigV o;
+  o.e.j2_clamped = negative(v.J2);
+  o.e.d_clamped = negative(v.D);
+  const double J2p = nonneg(v.J2);
+  const double Dp = nonneg(v.D);
+  o.m = sqrt_nonneg_split<3>(J2p, o.kr);
+  triple_angle_sines(v.J3, sqrt_nonneg(Dp * kInv27), o.e.sigma1, o.e.sigma2);
+  o.kKm = kK * o.m;
+  // k = kK r of A itself = kK m 2^(kr + e): for unscaled data (e = 0) the
+  // exponent is added on the integer pipe (kK m 2^kr is a normal number:
+  // J2+ >= 2^-1074 keeps r above 2^-537), otherwise by exact multiplications
+  // that over- or underflow like the product itself
+  const double k =
+      (v.e == 0) ? times_pow2(o.kKm, o.kr) : o.kKm * pow2d(o.kr) * pow2d(v.e);
+  o.e.r = o.m;  // r of the scaled data up to 2^kr (the fused kernel stores no r)
+  const double i3 = v.I1 * kInv3;
+  o.c12 = fma(2.0, o.e.sigma1, o.e.sigma2);
+  o.e.l1 = fma(-k, o.c12, i3);
+  o.e.l2 = fma(k, o.e.sigma1 - o.e.sigma2, i3);
+  o.e.l3 = fma(k, fma(2.0, o.e.sigma2, o.e.sigma1), i3);
+  return o;
+}
+
+// The adjoint scalars of adjoint_scalars (a_I1, a_J2 2^kr, a_J3 2^2kr, in
+// the scaled frame) from the forward's m, kr, kK m and 2 sigma1 + sigma2:
+//   D23 = n23 s1 (s3 Rh),  D23 - D12 = D23 - n12 s2 (s3 Rh),
+//   a_J3 2^2k = (D23 - D12) s1 s2 Rh,  a_J2 2^k = D23 - kK m (2 s1 + s2) a_J3 2^2k,
+// with Rh = (sqrt3/2) / (m s1 s2 s3), and a_I1 = g2 + (n23 - n12)/3.
+__device__ __forceinline__ Adj adjoint_vjp(const EigV &f, double g1, double g2, double g3) {
+  const double sigma1 = f.e.sigma1, sigma2 = f.e.sigma2;
+  const bool z1 = hi_abs(sigma1) < (63 << 20);
+  const bool z2 = hi_abs(sigma2) < (63 << 20);
+  const double s1 = z1 ? 1.0 : sigma1, s2 = z2 ? 1.0 : sigma2;
+  const double s3 = sigma1 + sigma2;
+  const bool rz = hi_abs(f.m) < (1 << 20);  // r = 0: a triple eigenvalue
+  const double m = rz ? 1.0 : f.m;
+  const double s12 = s1 * s2;
+  const double P = s12 * s3;
+  const double R = recip_pos(m * P);
+  const double Rh = kHalfSqrt3 * R;
+  double n12 = g2 - g1, n23 = g3 - g2;
+  Adj o;
+  o.aI1 = fma(n23 - n12, kInv3, g2);
+  if (z1 || z2) {  // an exactly coalesced pair takes the mean of its two weights
+    n12 = z1 ? 0.0 : 0.5 * (g2 + g3) - g1;
+    n23 = z2 ? 0.0 : g3 - 0.5 * (g1 + g2);
+  }
+  const double s3Rh = s3 * Rh;
+  const double D23 = n23 * (s1 * s3Rh);
+  const double aJ3s = fma(-(n12 * s2), s3Rh, D23) * (s12 * Rh);
+  const double aJ2s = fma(-(f.kKm * f.c12), aJ3s, D23);
+  o.aJ2s = rz ? 0.0 : aJ2s;
+  o.aJ3s = rz ? 0.0 : aJ3s;
+  o.k = rz ? 0 : f.kr;
+  o.rz = rz;
+  return o;
+}
+
+// b2 = a_J2, b3 = a_J3 of the scaled frame from the carried a_J2 2^k and
+// a_J3 2^2k, as grad_units does it but without a branch: while they and the
+// scaled deviatoric data stay inside 2^+-448 (always, but for J2 tiny against
+// the data of a nearly defective matrix), b2 = a_J2 2^k 2^-k and b3 = a_J3
+// 2^2k 2^-2k; otherwise b2, b3 stay as carried and the data and products are
+// shifted by 2^-k and 2^-2k instead.  The shift returned (0 in range) is
+// applied by exponent arithmetic (times_pow2), so both cases run the same
+// FP64 instructions and no lane idles on the other case's.
+__device__ __forceinline__ int vjp_units(const Adj &s, int hmax, double &b2, double &b3) {
+  const int E = hmax >> 20;
+  const bool in_range = E >= 1023 - 448 && E <= 1023 + 448 && s.k >= -448 && s.k <= 448;
+  const double u2 = s.aJ2s * pow2d(in_range ? -s.k : 0);
+  const double u3 = s.aJ3s * pow2d(in_range ? -2 * s.k : 0);
+  b2 = u2;
+  b3 = u3;
+  return in_range ? 0 : -s.k;
+}
+
+// Gradient of a general matrix from the fused adjoint, G[0..8] row-major
+// (as grad_general: a_I1 I + a_J2 dev(A)^T + a_J3 dev(cof dev A)).
+__device__ __forceinline__ void grad_general_vjp(const ShareG &x, double J2, const Adj &s,
+                                                 double (&G)[9]) {
+  double D[9] = {x.tn * kInv3, x.a01, x.a02, x.a10, -(x.t2 * kInv3), x.a12, x.a20, x.a21,
+                 -(x.t1 * kInv3)};
+  int h = hi_abs(D[0]);
+#pragma unroll
+  for (int j = 1; j < 9; ++j) h = max(h, hi_abs(D[j]));
+  double b2, b3;
+  const int sh = vjp_units(s, h, b2, b3);
+  double P[10] = {x.p12, x.m2012, x.m1021, x.m0221, x.p02, x.m2001, x.m0112, x.m0210, x.p01, J2};
+  if (sh != 0) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) D[j] = times_pow2_sat(D[j], sh);
+#pragma unroll
+    for (int j = 0; j < 10; ++j) P[j] = times_pow2_sat(P[j], 2 * sh);
+  }
+  double C[9];
+  C[0] = fma(D[4], D[8], -P[0]);
+  C[1] = fma(-D[3], D[8], P[1]);
+  C[2] = fma(-D[4], D[6], P[2]);
+  C[3] = fma(-D[1], D[8], P[3]);
+  C[4] = fma(D[0], D[8], -P[4]);
+  C[5] = fma(-D[0], D[7], P[5]);
+  C[6] = fma(-D[2], D[4], P[6]);
+  C[7] = fma(-D[0], D[5], P[7]);
+  C[8] = fma(D[0], D[4], -P[8]);
+  const double base = fma(b3, P[9] * kInv3, s.aI1);  // -a_J3 tr(cof S) / 3
+  G[0] = fma(b2, D[0], fma(b3, C[0], base));
+  G[1] = fma(b2, D[3], b3 * C[1]);
+  G[2] = fma(b2, D[6], b3 * C[2]);
+  G[3] = fma(b2, D[1], b3 * C[3]);
+  G[4] = fma(b2, D[4], fma(b3, C[4], base));
+  G[5] = fma(b2, D[7], b3 * C[5]);
+  G[6] = fma(b2, D[2], b3 * C[6]);
+  G[7] = fma(b2, D[5], b3 * C[7]);
+  G[8] = fma(b2, D[8], fma(b3, C[8], base));
+}
+
+// The symmetric form (gradient with respect to the six stored entries, as
+// grad_sym), cofactors C00 = S11 S22 - c^2, C12 = ab - S00 c, ... on the
+// products of invariants_sym.
+__device__ __forceinline__ void grad_sym_vjp(const ShareS &x, double J2, const Adj &s,
+                                             double (&G)[6]) {
+  double D[6] = {x.tn * kInv3, -(x.t2 * kInv3), -(x.t1 * kInv3), x.c, x.b, x.a};
+  int h = hi_abs(D[0]);
+#pragma unroll
+  for (int j = 1; j < 6; ++j) h = max(h, hi_abs(D[j]));
+  double b2, b3;
+  const int sh = vjp_units(s, h, b2, b3);
+  double P[7] = {x.cc, x.bb, x.aa, x.ab, x.ac, x.bc, J2};
+  if (sh != 0) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) D[j] = times_pow2_sat(D[j], sh);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) P[j] = times_pow2_sat(P[j], 2 * sh);
+  }
+  const double S00 = D[0], S11 = D[1], S22 = D[2];
+  const double C00 = fma(S11, S22, -P[0]);
+  const double C11 = fma(S00, S22, -P[1]);
+  const double C22 = fma(S00, S11, -P[2]);
+  const double C12 = fma(-S00, D[3], P[3]);
+  const double C02 = fma(-S11, D[4], P[4]);
+  const double C01 = fma(-S22, D[5], P[5]);
+  const double base = fma(b3, P[6] * kInv3, s.aI1);
+  const double b2x2 = 2.0 * b2, b3x2 = 2.0 * b3;
+  G[0] = fma(b2, D[0], fma(b3, C00, base));
+  G[1] = fma(b2, D[1], fma(b3, C11, base));
+  G[2] = fma(b2, D[2], fma(b3, C22, base));
+  G[3] = fma(b2x2, D[3], b3x2 * C12);
+  G[4] = fma(b2x2, D[4], b3x2 * C02);
+  G[5] = fma(b2x2, D[5], b3x2 * C01);
 }
 
 }  // namespace eig3

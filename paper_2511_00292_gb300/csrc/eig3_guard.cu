@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads)
       q[3] = (T)((a[0] + a[4]) + a[8]);
     }
     if constexpr (STATS) {
-      stat_add(acc, e.d_clamped, e.j2_clamped, e.r > 0.0,
+      stat_add(acc, e.d_clamped, e.j2_clamped, __double_as_longlong(e.r) > 0,
                seed_float(min_nonneg(e.sigma1, e.sigma2)), (T)e.l1, (T)e.l2, (T)e.l3);
     }
   });

@@ -28,6 +28,8 @@ cudaError_t launch_mohr_coulomb_f64(const void *A, int layout, int dtype, int64_
                                     double m, void *f, void *grad_A, cudaStream_t s);
 cudaError_t launch_variant_f64(const void *A, int layout, int dtype, int variant, int64_t n,
                                double *inv, void *lam, cudaStream_t s);
+cudaError_t launch_eigvals_vjp_f64(const void *A, int layout, int dtype, int64_t n, const void *w,
+                                   void *lam, void *grad_A, eig3_stats *stats, cudaStream_t s);
 cudaError_t launch_backward_f64(const void *A, int layout, int dtype, int64_t n,
                                 const void *grad_lam, const void *aux, void *grad_A,
                                 cudaStream_t s);
@@ -41,6 +43,8 @@ cudaError_t launch_projectors_f32c(const void *A, int layout, int64_t n, void *l
                                    cudaStream_t s);
 cudaError_t launch_mohr_coulomb_f32c(const void *A, int layout, int64_t n, double s_yc, double m,
                                      void *f, void *grad_A, cudaStream_t s);
+cudaError_t launch_eigvals_vjp_f32c(const void *A, int layout, int64_t n, const void *w, void *lam,
+                                    void *grad_A, eig3_stats *stats, cudaStream_t s);
 cudaError_t launch_backward_f32c(const void *A, int layout, int64_t n, const void *grad_lam,
                                  const void *aux, void *grad_A, cudaStream_t s);
 

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads)
     if constexpr (LAYOUT == EIG3_GENERAL9) {
       v = invariants_general_c(a);
     } else {
-      v = invariants_sym_c(a[0], a[1], a[2], a[3], a[4], a[5]);
+      v = invariants_sym_c<true>(a[0], a[1], a[2], a[3], a[4], a[5]);
     }
     const EigC e = eigvals_c(v);
     f[i] = fmaf(cm, e.l3, fmaf(-c1, e.l1, -1.0f));

@@ -127,4 +127,80 @@ __device__ __forceinline__ void for_each_row(const T *__restrict__ A, int64_t n,
                             });
 }
 
+// ---------------------------------------------------------------------------
+// Warp-granular staging: each warp walks the batch in tiles of 32 rows
+// (grid-stride over the grid's warps) with a double buffer of its own in
+// shared memory, waiting only on its own copies (cp.async.wait_group, then
+// __syncwarp, which also orders the lanes' shared-memory accesses).  No block
+// barrier, so the warps of a block drift apart instead of meeting once per
+// tile: for the FP64-bound kernels the phases with little binary64 work (the
+// seeds of the square roots and the angle, the stores) of different warps
+// then overlap the binary64 work of others.  A warp tile starts at element
+// 32 W t of its array, a multiple of 16 bytes for W = 3, 6, 9 and 4- or
+// 8-byte elements, so its full 16-byte chunks are aligned whenever the base is.
+// ---------------------------------------------------------------------------
+constexpr int kWarpTile = 32;
+
+template <typename E>
+__device__ __forceinline__ void warp_tile_issue(const E *__restrict__ g, int64_t e0, int count,
+                                                E *__restrict__ s, int lane) {
+  const E *src = g + e0;
+  int head = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    const int n16 = (count * (int)sizeof(E)) >> 4;
+    const char *s8 = reinterpret_cast<const char *>(src);
+    char *d8 = reinterpret_cast<char *>(s);
+    for (int i = lane; i < n16; i += 32) cp_async16(d8 + 16 * i, s8 + 16 * i);
+    head = (n16 << 4) / (int)sizeof(E);
+  }
+  for (int i = head + lane; i < count; i += 32) s[i] = __ldg(src + i);
+}
+
+// Calls body(i, rowA, rowB) for every row i of the batch that falls to this
+// lane: rowA points at the N elements of row i of A in shared memory and rowB
+// (M > 0) at the M elements of row i of B.  wA / wB are this warp's two
+// buffers (kWarpTile rows each).  Every lane of the warp must call it.
+template <int N, int M, typename T, typename U, typename Body>
+__device__ __forceinline__ void for_each_row_warp2(const T *__restrict__ A,
+                                                   const U *__restrict__ B, int64_t n,
+                                                   T (*wA)[kWarpTile * N],
+                                                   U (*wB)[kWarpTile * (M > 0 ? M : 1)],
+                                                   Body body) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ntiles = (n + kWarpTile - 1) / kWarpTile;
+  const int64_t first = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5);
+  auto rows_of = [&](int64_t t) { return (int)min((int64_t)kWarpTile, n - t * kWarpTile); };
+  auto issue = [&](int64_t t, int b) {
+    warp_tile_issue(A, t * kWarpTile * N, rows_of(t) * N, wA[b], lane);
+    if constexpr (M > 0) warp_tile_issue(B, t * kWarpTile * M, rows_of(t) * M, wB[b], lane);
+  };
+  int buf = 0;
+  if (first < ntiles) issue(first, 0);
+  cp_async_commit();
+  for (int64_t t = first; t < ntiles; t += step) {
+    cp_async_wait_all();
+    __syncwarp();  // tile t has landed; every lane is done with the other buffer
+    const int64_t tn = t + step;
+    if (tn < ntiles) issue(tn, buf ^ 1);
+    cp_async_commit();
+    if (lane < rows_of(t)) {
+      if constexpr (M > 0) {
+        body(t * kWarpTile + lane, wA[buf] + lane * N, wB[buf] + lane * M);
+      } else {
+        body(t * kWarpTile + lane, wA[buf] + lane * N, (const U *)nullptr);
+      }
+    }
+    buf ^= 1;
+  }
+}
+
+// One input array: body(i, row).
+template <int N, typename T, typename Body>
+__device__ __forceinline__ void for_each_row_warp(const T *__restrict__ A, int64_t n,
+                                                  T (*wA)[kWarpTile * N], Body body) {
+  for_each_row_warp2<N, 0, T, T>(A, (const T *)nullptr, n, wA, (T(*)[kWarpTile])nullptr,
+                                 [&](int64_t i, const T *row, const T *) { body(i, row); });
+}
+
 }  // namespace eig3

@@ -23,7 +23,7 @@ import mmap
 
 import torch
 
-from . import eigvals, eigvals_backward, layout_of
+from . import eigvals, eigvals_backward, eigvals_vjp, layout_of
 
 
 class _PinnedMap(mmap.mmap):
@@ -176,9 +176,14 @@ class HostPipeline:
                     slots["loaded"][k].record(self.s_in)
                 with torch.cuda.stream(self.s_run):
                     self.s_run.wait_event(slots["loaded"][k])
-                    eigvals(dA, layout=lay, precision=precision, return_aux=True, out=dl,
-                            aux_out=da)
-                    eigvals_backward(dA, dw, aux=da, layout=lay, precision=precision, out=dg)
+                    if precision in ("f64", "f32c"):  # fused forward + vector-Jacobian product
+                        eigvals_vjp(dA, dw, layout=lay, precision=precision, out=dl,
+                                    grad_out=dg)
+                    else:
+                        eigvals(dA, layout=lay, precision=precision, return_aux=True, out=dl,
+                                aux_out=da)
+                        eigvals_backward(dA, dw, aux=da, layout=lay, precision=precision,
+                                         out=dg)
                     slots["done"][k].record(self.s_run)
                 with torch.cuda.stream(self.s_out):
                     self.s_out.wait_event(slots["done"][k])

@@ -28,7 +28,8 @@ def declared_functions():
 
 def test_header_declares_the_api():
     names = declared_functions()
-    for n in ("eig3_invariants", "eig3_eigvals", "eig3_eigvals_backward", "eig3_eigprojectors",
+    for n in ("eig3_invariants", "eig3_eigvals", "eig3_eigvals_backward", "eig3_eigvals_vjp",
+              "eig3_eigprojectors",
               "eig3_mohr_coulomb", "eig3_eigvals_variant", "eig3_stats_reset",
               "eig3_status_string", "eig3_version"):
         assert n in names
@@ -49,7 +50,7 @@ def test_library_is_sm_103a_and_static_runtime():
 
 
 def test_version_and_status_strings(lib):
-    assert lib.eig3_version() == 10200
+    assert lib.eig3_version() == 10300
     assert lib.eig3_status_string(0) == b"EIG3_OK"
     for code in range(1, 6):
         assert lib.eig3_status_string(code).startswith(b"EIG3_ERR")
@@ -136,6 +137,21 @@ def test_host_validation_without_gpu(lib):
     assert var(ok_ptr, 0, 1, 2, 5, None, P(0x10002), None) == 4
     assert var(ok_ptr, 3, 0, 1, 5, ok_ptr, None, None) == 2
     assert var(ok_ptr, 0, 2, 1, 5, ok_ptr, None, None) == 3
+    # fused forward + vector-Jacobian product
+    vjp = lib.eig3_eigvals_vjp
+    assert vjp(None, 0, 0, 0, 0, None, None, None, None, None) == 0
+    assert vjp(ok_ptr, 0, 0, 0, 5, None, None, ok_ptr, None, None) == 1        # no weights
+    assert vjp(ok_ptr, 0, 0, 0, 5, ok_ptr, None, None, None, None) == 1        # no gradient
+    assert vjp(None, 0, 0, 0, 5, ok_ptr, None, ok_ptr, None, None) == 1
+    assert vjp(ok_ptr, 0, 0, 0, 5, bad_ptr, None, ok_ptr, None, None) == 4
+    assert vjp(ok_ptr, 0, 0, 0, 5, ok_ptr, bad_ptr, ok_ptr, None, None) == 4   # lam optional
+    assert vjp(ok_ptr, 0, 0, 0, 5, ok_ptr, None, ok_ptr, P(0x10004), None) == 4
+    assert vjp(ok_ptr, 1, 1, 1, 5, ok_ptr, None, P(0x10002), None, None) == 4
+    assert vjp(ok_ptr, 0, 0, 1, 5, ok_ptr, None, ok_ptr, None, None) == 3      # F64 + F32_COMP
+    assert vjp(ok_ptr, 0, 0, 2, 5, ok_ptr, None, ok_ptr, None, None) == 3      # guarded
+    assert vjp(ok_ptr, 1, 1, 3, 5, ok_ptr, None, ok_ptr, None, None) == 3      # f32c64
+    assert vjp(ok_ptr, 4, 0, 0, 5, ok_ptr, None, ok_ptr, None, None) == 2
+    assert vjp(ok_ptr, 0, 0, 0, -3, ok_ptr, None, ok_ptr, None, None) == 1
     # stats reset
     assert lib.eig3_stats_reset(None, None) == 1
     assert lib.eig3_stats_reset(P(0x10004), None) == 4

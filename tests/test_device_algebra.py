@@ -239,7 +239,8 @@ def device_function(name, path=None, env=None, types=TYPES, ctors=None, braces="
 
 BASE_ENV = dict(
     _Q=sp.Rational, NS=NS, fma=lambda a, b, c: a * b + c,
-    recip_pos=lambda x: 1 / x, pow2d=lambda k: sp.Integer(2) ** k, **EXACT)
+    recip_pos=lambda x: 1 / x, pow2d=lambda k: sp.Integer(2) ** k,
+    times_pow2=lambda x, k: x * sp.Integer(2) ** k, **EXACT)
 BASE_ENV["dx13"] = lambda *a: device_function("dx13")(*a)
 
 
@@ -306,20 +307,35 @@ def test_invariants_sym_source_equals_definitions():
 
 
 def test_delta_terms_carry_the_paper_weights():
-    """A plausible slip (a wrong weight of one product group, or r1 of dx(A^T)
-    taken with the wrong sign) breaks the identity above: the check is not
-    vacuous.  Altering one weight in the translated source must fail it."""
+    """A plausible slip (a wrong weight of one product group -- the factor
+    8 applied as 2^3 to u5, the factor 2 as 2^1 to u13, the 6 of the last
+    group -- or r1 of dx(A^T) taken with the wrong sign, or J3's mixed term
+    regrouped with the wrong difference) breaks the identities above: the
+    checks are not vacuous.  Altering one of them in the translated source
+    must fail it."""
     a, A = general_symbols()
     fn = device_function("invariants_general")
     src_code = fn.code
-    assert "_Q('8.0')" in src_code and "-_Q('9.0') * r1" in src_code
-    for old, new in (("_Q('8.0')", "_Q('6.0')"), ("-_Q('9.0') * r1", "_Q('9.0') * r1")):
+    slips = (("times_pow2(u.r5, 3)", "times_pow2(u.r5, 2)"),
+             ("times_pow2(u.r13, 1)", "times_pow2(u.r13, 0)"),
+             ("fma(_Q('6.0'),", "fma(_Q('8.0'),"),
+             ("-_Q('9.0') * r1", "_Q('9.0') * r1"))
+    for old, _ in slips:
+        assert old in src_code, old
+    for old, new in slips:
         env = dict(BASE_ENV)
         env["a"] = a
         exec(src_code.replace(old, new, 1), env)
         o = env["__ret__"]
         _, J2, J3 = invariants_of(A)
         assert not zero(o.D - (4 * J2 ** 3 - 27 * J3 ** 2))
+    # J3 with e9 for e8 in its mixed term
+    assert "fma(t2, tn * kInv9, s.e8)" in src_code
+    env = dict(BASE_ENV)
+    env["a"] = a
+    exec(src_code.replace("fma(t2, tn * kInv9, s.e8)", "fma(t2, tn * kInv9, s.e9)", 1), env)
+    _, J2, J3 = invariants_of(A)
+    assert not zero(env["__ret__"].J3 - J3)
 
 
 def _roots_derivatives(r, s1, s2, g):
@@ -474,6 +490,9 @@ def f32c_function(name, **fixed):
 
 ENV_C["diag_parts"] = lambda *a: f32c_function("diag_parts")(*a)
 ENV_C["dx_c"] = lambda *a: f32c_function("dx_c")(*a)
+ENV_C["sq1"] = lambda r: val(r) ** 2
+ENV_C["disc_sym_compensated"] = lambda *a: f32c_function("disc_sym_compensated")(*a)
+ENV_C["disc_sym_rounded"] = lambda *a: f32c_function("disc_sym_rounded")(*a)
 
 
 def _check_scaled_invariants(o, A):
@@ -485,12 +504,33 @@ def _check_scaled_invariants(o, A):
     assert zero(val(o.D) - (4 * J2 ** 3 - 27 * J3 ** 2))
 
 
-def test_compensated_invariants_sym_source_equals_definitions():
+@pytest.mark.parametrize("eig", [False, True])
+def test_compensated_invariants_sym_source_equals_definitions(eig):
     """The symmetric compensated invariants (Algorithms 1, 2, 4, 5 with the
     symmetric identities and reading R1, every r_i summed term by term) are
-    I1, 6 J2, 27 J3 and the discriminant exactly."""
+    I1, 6 J2, 27 J3 and the discriminant exactly -- with the discriminant
+    finished either way (compensated for the invariants output, the rounded
+    non-negative sum for the eigenvalue kernels)."""
     s6, A = sym_symbols()
-    _check_scaled_invariants(f32c_function("invariants_sym_c")(*s6), A)
+    _check_scaled_invariants(f32c_function("invariants_sym_c", EIG=eig)(*s6), A)
+
+
+def test_rounded_discriminant_keeps_the_weights():
+    """A wrong weight in the rounded form (2 for 14, or a dropped r14^2)
+    breaks the identity: the check above is not vacuous for it."""
+    s6, A = sym_symbols()
+    fn = f32c_function("disc_sym_rounded")
+    code = fn.code
+    for old, new in (("_Q('14.0')", "_Q('2.0')"), ("sq1(r14)", "_Q('0.0')")):
+        assert old in code
+    r = sp.symbols("r2 r3 r4 r8 r9 r10 r11 r12 r13 r14")
+    want = 14 * (r[0] ** 2 + r[1] ** 2 + r[2] ** 2) + 2 * sum(x ** 2 for x in r[3:9]) + r[9] ** 2
+    assert zero(val(fn(*r)) - want)
+    for old, new in (("_Q('14.0')", "_Q('2.0')"), ("sq1(r14)", "_Q('0.0')")):
+        e = dict(ENV_C)
+        e.update(zip(["r2", "r3", "r4", "r8", "r9", "r10", "r11", "r12", "r13", "r14"], r))
+        exec(code.replace(old, new, 1), e)
+        assert not zero(val(e["__ret__"]) - want)
 
 
 def test_compensated_invariants_general_source_equals_definitions():

@@ -326,7 +326,10 @@ def test_huge_page_pinned_buffers(eig3):
     grad = host.pinned_empty(hA.shape, torch.float64)
     HostPipeline(dev(), chunk=4096, depth=3).forward_backward(hA, hw, lam, grad)
     torch.cuda.synchronize()
-    assert torch.equal(lam, l_d.cpu()) and torch.equal(grad, g_d.cpu())
+    # the pipeline runs the fused kernel (eig3_eigvals_vjp)
+    lv, gv = eig3.eigvals_vjp(dA, bt.extra["w"].to(dev()))
+    assert torch.equal(lam, l_d.cpu()) and torch.equal(lam, lv.cpu())
+    assert torch.equal(grad, gv.cpu())
     for _ in range(8):
         x = host.pinned_empty((1 << 24,), torch.float64)   # 128 MiB each
         x[::4096].fill_(1.0)
@@ -339,8 +342,9 @@ def test_huge_page_pinned_buffers(eig3):
 
 @pytest.mark.parametrize("depth", [2, 3])
 def test_host_pipeline_matches_device(eig3, depth):
-    """Chunked host-to-device streaming gives the device results bit for bit,
-    including a ragged last chunk and more chunks than device slots."""
+    """Chunked host-to-device streaming gives the device results (of the fused
+    kernel it runs) bit for bit, including a ragged last chunk and more chunks
+    than device slots."""
     from paper_2511_00292_gb300.host import HostPipeline
     bt = W.workload4(n=10_007, device="cpu", seed=2200)
     hA, hw = bt.A.pin_memory(), bt.extra["w"].pin_memory()
@@ -350,8 +354,7 @@ def test_host_pipeline_matches_device(eig3, depth):
     pipe.forward_backward(hA, hw, lam, grad)
     torch.cuda.synchronize()
     dA = bt.A.to(dev())
-    l_d, a_d = eig3.eigvals(dA, return_aux=True)
-    g_d = eig3.eigvals_backward(dA, bt.extra["w"].to(dev()), aux=a_d)
+    l_d, g_d = eig3.eigvals_vjp(dA, bt.extra["w"].to(dev()))   # the kernel the pipeline runs
     assert torch.equal(lam, l_d.cpu()) and torch.equal(grad, g_d.cpu())
     S = W.workload3(n=5_003, device="cpu", seed=2201).A
     wS = torch.randn(S.shape[0], 3, dtype=torch.float32)
@@ -359,8 +362,7 @@ def test_host_pipeline_matches_device(eig3, depth):
     gS = torch.empty_like(S).pin_memory()
     pipe.forward_backward(S.pin_memory(), wS.pin_memory(), lS, gS, precision="f32c")
     torch.cuda.synchronize()
-    l2, a2 = eig3.eigvals(S.to(dev()), precision="f32c", return_aux=True)
-    g2 = eig3.eigvals_backward(S.to(dev()), wS.to(dev()), aux=a2, precision="f32c")
+    l2, g2 = eig3.eigvals_vjp(S.to(dev()), wS.to(dev()), precision="f32c")
     assert torch.equal(lS, l2.cpu()) and torch.equal(gS, g2.cpu())
 
 

@@ -1,10 +1,12 @@
 """The benchmark's step at its full size, in its launch configuration: the
 mixed workload of 2^28 matrices (2^27 symmetric binary32 through the
-compensated kernels, 2^27 general binary64 through the binary64 kernels),
-forward + adjoint with the binary32 pair on a second stream beside the
-binary64 pair, run three times (statistics over the last two).  Sampled outputs of
-both halves are compared with the oracle (eigenvalues and eigenvector-form
-gradients), and the statistics with properties that hold at any size."""
+compensated kernel, 2^27 general binary64 through the binary64 kernel),
+forward + vector-Jacobian product fused per half (eig3_eigvals_vjp) with the
+binary32 launch on a second stream beside the binary64 one, run three times
+(statistics over the last two).  Sampled outputs of both halves are compared
+with the oracle (eigenvalues on 2^20 samples per half, eigenvector-form
+gradients on 2^18), and the statistics with properties that hold at any
+size."""
 import numpy as np
 import pytest
 import torch
@@ -36,10 +38,8 @@ def test_full_size_mixed_step(eig3):
     w5 = W.workload5(n=1 << 28, device=dev)
     S, G = w5["sym6"], w5["general9"]
     lamS = torch.empty(S.n, 3, dtype=torch.float32, device=dev)
-    auxS = torch.empty(S.n, 4, dtype=torch.float32, device=dev)
     gS = torch.empty_like(S.A)
     lamG = torch.empty(G.n, 3, dtype=torch.float64, device=dev)
-    auxG = torch.empty(G.n, 4, dtype=torch.float64, device=dev)
     gG = torch.empty_like(G.A)
     st = eig3.Stats(dev)
     s64, s32 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -49,12 +49,10 @@ def test_full_size_mixed_step(eig3):
         s64.wait_stream(cur)
         s32.wait_stream(cur)
         with torch.cuda.stream(s64):
-            eig3.eigvals(G.A, precision="f64", return_aux=True, out=lamG, aux_out=auxG, stats=st)
-            eig3.eigvals_backward(G.A, G.extra["w"], aux=auxG, precision="f64", out=gG)
+            eig3.eigvals_vjp(G.A, G.extra["w"], precision="f64", out=lamG, grad_out=gG, stats=st)
         with torch.cuda.stream(s32):
-            eig3.eigvals(S.A, precision="f32c", return_aux=True, out=lamS, aux_out=auxS,
-                         stats=st)
-            eig3.eigvals_backward(S.A, S.extra["w"], aux=auxS, precision="f32c", out=gS)
+            eig3.eigvals_vjp(S.A, S.extra["w"], precision="f32c", out=lamS, grad_out=gS,
+                             stats=st)
         cur.wait_stream(s64)
         cur.wait_stream(s32)
 
@@ -71,12 +69,14 @@ def test_full_size_mixed_step(eig3):
     assert stats["max_abs_lambda"] == pytest.approx(maxabs, rel=1e-6)
 
     # binary64 half: eigenvalues and gradients on samples
-    idx = torch.as_tensor(W.sample_indices(G.n, 4096, seed=9201), device=dev)
+    idx = torch.as_tensor(W.sample_indices(G.n, 1 << 20, seed=9201), device=dev)
     XG = U.to_np(G.A[idx])
     kG = U.to_np(G.kappa[idx])
     err, tol, bad = U.check_eig_f64(U.to_np(lamG[idx]), XG, kG, GEN)
-    print(f"[full step] binary64 eigenvalues: max err/tol {np.max(err / tol):.3g}")
+    print(f"[full step] binary64 eigenvalues on {idx.numel()}: max err/tol {np.max(err / tol):.3g}")
     assert not bad.any()
+    idx = idx[:1 << 18]
+    XG, kG = XG[:1 << 18], kG[:1 << 18]
     wG = U.to_np(G.extra["w"][idx])
     lam_ref = oracle.eigvals(XG)
     sel = rel_gap(lam_ref) >= 1e-4
@@ -90,11 +90,13 @@ def test_full_size_mixed_step(eig3):
     assert np.all(gerr <= gtol)
 
     # compensated binary32 half
-    idx = torch.as_tensor(W.sample_indices(S.n, 4096, seed=9202), device=dev)
+    idx = torch.as_tensor(W.sample_indices(S.n, 1 << 20, seed=9202), device=dev)
     XS = U.to_np(S.A[idx])
     err, tol, _ = U.check_eig_f32c(U.to_np(lamS[idx]), XS, 1.0, SYM)
-    print(f"[full step] binary32 eigenvalues: max err/tol {np.max(err / tol):.3g}")
+    print(f"[full step] binary32 eigenvalues on {idx.numel()}: max err/tol {np.max(err / tol):.3g}")
     assert np.all(err <= tol)
+    idx = idx[:1 << 18]
+    XS = XS[:1 << 18]
     wS = U.to_np(S.extra["w"][idx])
     lam_ref = oracle.eigvals(XS, layout=SYM)
     sel = rel_gap(lam_ref) >= 1e-3

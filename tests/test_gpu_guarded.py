@@ -159,3 +159,50 @@ def test_binary32_storage_and_backward(eig3):
     g2 = eig3.eigvals_backward(A, w, precision="f64g")
     assert torch.equal(g1, g2)
     assert torch.isfinite(g1[torch.as_tensor(ok, device=dev())]).all()
+
+
+def test_switched_adjoint_against_lapack_eigenvectors(eig3):
+    """The adjoint on the rows the guard switches to QR (strongly non-normal,
+    kappa up to 1e4): the chain-rule gradient from the QR eigenvalue gaps
+    against d lambda_k / dA_ij = (V^-1)_ki V_jk from LAPACK's eigenvectors V,
+    where the spectrum is real and the relative gap >= 1e-4.  The oracle's
+    own eigenvector form is not used here: it starts from the closed-form
+    eigenvalues, which are what lose accuracy on these matrices.  Tolerance:
+    the gradient's sensitivity, kappa^2 (1 + ||A|| / gap) u per unit weight,
+    with the divided differences' own amplification (||A|| / gap)^2."""
+    bt = W.illconditioned(20_000, "cpu", seed=9106, log10_kappa_max=4.0)
+    X = bt.A.numpy()
+    S = X.reshape(-1, 3, 3) - np.einsum("nii->n", X.reshape(-1, 3, 3))[:, None, None] / 3 * np.eye(3)
+    fro2 = (S * S).sum(axis=(1, 2))
+    trS2 = np.einsum("nij,nji->n", S, S)
+    switched = fro2 > 40.0 * np.maximum(trS2, 0.0)          # beyond the guard's 32, with margin
+    ex = oracle.eigvals_exact(X[switched])
+    real = np.all(np.isfinite(ex), axis=1)
+    scale = np.abs(ex).max(axis=1)
+    gap = np.minimum(ex[:, 1] - ex[:, 0], ex[:, 2] - ex[:, 1])
+    sel = real & (gap >= 1e-4 * scale)
+    idx = np.nonzero(switched)[0][sel]
+    assert idx.size > 500
+    A = torch.as_tensor(X[idx], device=dev())
+    w = torch.randn(idx.size, 3, dtype=torch.float64, device=dev(),
+                    generator=torch.Generator(dev()).manual_seed(11))
+    st = eig3.Stats(dev())
+    lam, aux = eig3.eigvals(A, precision="f64g", return_aux=True, stats=st)
+    assert st.read()["n_guarded"] == idx.size
+    G = U.to_np(eig3.eigvals_backward(A, w, aux=aux, precision="f64g"))
+    wn = w.cpu().numpy()
+    M = X[idx].reshape(-1, 3, 3)
+    ev, V = np.linalg.eig(M)
+    order = np.argsort(ev.real, axis=1)
+    ev = np.take_along_axis(ev, order, axis=1)
+    V = np.take_along_axis(V, order[:, None, :], axis=2)
+    Vi = np.linalg.inv(V)
+    ref = np.einsum("nk,nki,njk->nij", wn, Vi, V).real.reshape(-1, 9)
+    nA = np.linalg.norm(X[idx], axis=1)
+    g = gap[sel]
+    k2 = bt.kappa.numpy()[idx] ** 2
+    tol = 64.0 * U.U64 * np.abs(wn).sum(axis=1) * (k2 * (1.0 + nA / g) + (nA / g) ** 2)
+    err = np.abs(G - ref).max(axis=1)
+    print(f"[guard] switched adjoint on {idx.size} rows: max err/tol {np.max(err / tol):.3g}, "
+          f"max |G| {np.abs(ref).max():.3g}")
+    assert np.all(err <= tol)

@@ -43,6 +43,10 @@ def test_every_entry_point_reports_a_failed_launch(lib):
         "eig3_eigvals guarded": lambda: lib.eig3_eigvals(ok, 0, 0, 2, 5, ok, None, None, None),
         "eig3_eigvals_backward": lambda: lib.eig3_eigvals_backward(ok, 0, 0, 0, 5, ok, ok, ok,
                                                                    None),
+        "eig3_eigvals_vjp f64": lambda: lib.eig3_eigvals_vjp(ok, 0, 0, 0, 5, ok, ok, ok, ok,
+                                                             None),
+        "eig3_eigvals_vjp f32c": lambda: lib.eig3_eigvals_vjp(ok, 1, 1, 1, 5, ok, None, ok, None,
+                                                              None),
         "eig3_eigprojectors": lambda: lib.eig3_eigprojectors(ok, 0, 0, 0, 5, ok, ok, None),
         "eig3_mohr_coulomb": lambda: lib.eig3_mohr_coulomb(ok, 1, 0, 0, 5, D(100.0), D(10.0),
                                                            ok, ok, None),
