@@ -2,20 +2,27 @@
 
 One step = one forward + backward pass of the whole path over the mixed
 workload of 2^28 matrices per GPU: 2^27 symmetric 6-entry binary32 matrices
-through the compensated binary32 kernels and 2^27 general 9-entry binary64
-matrices through the binary64 kernels (invariants I1, J2, J3, Delta ->
-triple angle -> eigenvalues -> adjoint), the two halves on two streams.
+through the compensated binary32 kernel and 2^27 general 9-entry binary64
+matrices through the binary64 kernel (invariants I1, J2, J3, Delta ->
+triple angle -> eigenvalues -> adjoint, fused in one pass per matrix:
+eig3_eigvals_vjp), the two halves on two streams.
 Inputs are resident in HBM and larger than L2 (about 18 GB per step), so no
 L2 flush is needed between steps.
 
 Printed (rank 0, one JSON line): whole-job throughput in G matrices/s, the
-roofline of the dominant kernel (binary64 general forward) measured live with
-CUDA events, per-path throughputs of the other workloads' shapes, the CPU
-oracle timed on the host cores on a bounded sample (with the max error over
-the stability bound of the GPU results on that sample), an end-to-end number
-through host buffers, and SM clocks sampled during the timed region.
+roofline of the dominant kernel (the fused binary64 kernel) and of the
+binary64 forward, both against FP64 / FP32 peaks measured in the same run by
+throughput loops, per-path throughputs of the other workloads' shapes (among
+them the step as one CUDA graph of 10 steps, and unfused), the CPU oracle
+timed on the host cores on a bounded sample (with the max error over the
+stability bound of the GPU results on that sample, and the distance of the
+GPU results from the exact eigenvalues and invariants per eigenvalue and
+per invariant), an end-to-end number through host buffers, and SM clocks
+sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --peaks            (the FP64 / FP32 pipe peaks alone)
+  python bench.py --only KERNEL --n N (one kernel alone, for profiler captures)
 """
 from __future__ import annotations
 
@@ -41,31 +48,69 @@ UNIT = "G matrices/s"
 N_MIXED = 1 << 28
 WORKLOAD = ("mixed fwd+bwd, 2^28 matrices/GPU: 2^27 symmetric 6-entry FP32 (compensated FP32 "
             "path) + 2^27 general 9-entry FP64 (FP64 path), scales 10^U[-8,8], 30% "
-            "triple-perturbed, the binary32 half on a second stream")
+            "triple-perturbed; loss sum(w lambda), w ~ N(0,1); forward and vector-Jacobian "
+            "product fused per half, the binary32 half on a second stream")
 
-# Per-matrix counts of the binary64 general 9-entry forward kernel with
-# adjoint outputs and statistics (the launch of the timed step), taken with ncu
-# on n = 2^22 (bench.py --only fwd_f64_general9): thread-level instructions on
-# the FP64 pipe, of which DFMA / DMUL / DADD, and DRAM bytes read + written.
-# They describe the kernel source whose hash is recorded here; when the source
-# changes they are reported as stale and the traffic as null.
-FWD_F64_COUNTERS = {
-    "source_md5": "037d9baa6a11164747fac4e74e25d8f1",
-    "fp64_pipe_inst": 171.10, "dfma": 84.0, "dmul": 63.0, "dadd": 17.0,
-    "dram_bytes": (302.036992e6 + 193.370112e6) / 4194304,
+# Per-matrix ncu counters of the two binary64 kernels whose rooflines the line
+# reports, each taken with ncu on n = 2^22 (bench.py --only NAME, the same
+# launch as in the timed step): thread-level instructions on the FP64 pipe
+# (active lanes only) and the warp-level count times 32 (what occupies the
+# pipe, idle lanes included), of which DFMA / DMUL / DADD, and DRAM bytes read
+# + written.  They describe the kernel source whose
+# hash is recorded; when the source changes they are reported as stale and
+# every figure derived from them as null.
+KERNEL_COUNTERS = {
+    "vjp_f64_general9": {
+        "source_md5": "172404f25be60f1556e7d34ffbe68b52",
+        "fp64_pipe_inst": 216.02, "fp64_warp_inst_x32": 227.49,
+        "dfma": 111.01, "dmul": 84.00, "dadd": 21.01,
+        "dram_bytes": (403.437056e6 + 352.872704e6) / 4194304,
+    },
+    "fwd_f64_general9": {
+        "source_md5": "752d29d2b5ac6e546e25ff8176b01773",
+        "fp64_pipe_inst": 160.00, "fp64_warp_inst_x32": 160.00,
+        "dfma": 83.00, "dmul": 61.00, "dadd": 16.00,
+        "dram_bytes": (302.145792e6 + 192.602880e6) / 4194304,
+    },
 }
-# the headers whole, and of eig3_f64.cu the forward kernel and its launchers
-FWD_F64_SOURCES = ("eig3_f64.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
-                   ("eig3_f64.cu", ("k_eigvals", "eig_launch4", "eig_launch")))
-# FP64 pipe of GB300: 2 FMA lanes per SM (measured with a DFMA loop: 0.598 T
-# DFMA/s at 1.97 GHz on 152 SMs), so the peak is SMs x 2 x clock instructions/s.
+# What each hash covers: the headers whole and, of eig3_f64.cu (which holds
+# other kernels too), the kernel's own definitions, its launchers and every
+# helper of that file they use (tests/test_bench_helpers.py checks the list
+# against the kernel bodies).
+KERNEL_SOURCES = {
+    "vjp_f64_general9": ("eig3_f64.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
+                         ("eig3_f64.cu", ("k_eigvals_vjp", "vjp_launch4", "vjp_launch", "Width"))),
+    "fwd_f64_general9": ("eig3_f64.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
+                         ("eig3_f64.cu", ("k_eigvals", "eig_launch4", "eig_launch", "store_aux",
+                                          "invariants_of", "aligned16", "Width"))),
+}
+# HBM bytes per matrix of the two kernels as launched in the step (algorithmic:
+# inputs read once, outputs written once)
+KERNEL_BYTES = {"vjp_f64_general9": 72 + 24 + 24 + 72, "fwd_f64_general9": 72 + 24 + 32}
+# The oracle's eigenvalue evaluation of a general matrix (Algorithms 1, 2, 4,
+# 5, 6 as the paper writes them, one rounded operation each), counted with the
+# op-counting scalar type of oracle/opcount.cpp (tests/test_oracle_opcount.py
+# pins these numbers): the method's literal arithmetic, before any sharing of
+# products or fusing into FMAs.
+ORACLE_OPS_EIGVALS_GENERAL9 = {"add": 112, "mul": 248, "div": 9, "neg": 7, "sqrt": 2,
+                               "atan2": 1, "cos": 3}
+# Nominal FP64 pipe of GB300: 2 fused multiply-adds per SM per clock.
 FP64_LANES_PER_SM = 2
 
 
 def _definitions(text, name):
-    """Source text of every definition (not a call) of function `name` in `text`,
-    from the start of its paragraph to its closing brace."""
+    """Source text of every definition (not a call) of function or struct
+    `name` in `text`, from the start of its paragraph to its closing brace."""
     out = []
+    for m in re.finditer(r"\bstruct\s+" + name + r"\s*\{", text):
+        depth, e = 0, m.end() - 1
+        for e in range(m.end() - 1, len(text)):
+            depth += text[e] == "{"
+            depth -= text[e] == "}"
+            if depth == 0:
+                break
+        start = text.rfind("\n\n", 0, m.start()) + 2
+        out.append(text[start:e + 1])
     for m in re.finditer(r"\b" + name + r"\s*\(", text):
         depth, k = 0, m.end() - 1
         for k in range(m.end() - 1, len(text)):  # the parameter list
@@ -305,6 +350,106 @@ def run_reference(args):
 # Our arm
 # --------------------------------------------------------------------------
 
+def measure_fp_peaks(dev, stream):
+    """Throughput of the binary64 and binary32 FMA pipes, measured here with the
+    loop kernels of libeig3_peaks.so: DFMA chains alone and between integer or
+    binary32 work (kinds 0, 4, 5), FFMA chains (kind 3), each over a few chain
+    counts and blocks per SM, about 30 ms per launch after a calibration
+    launch; the fastest of each pipe is its measured peak."""
+    import ctypes
+    from paper_2511_00292_gb300 import build as _b
+    lib = ctypes.CDLL(_b.PEAKS_LIB)
+    lib.eig3_peak_loop.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p, ctypes.c_void_p]
+    lib.eig3_peak_loop.restype = ctypes.c_int
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    runs = []
+
+    def one(kind, chains, bps, thr, target_ms):
+        blocks = sms * bps
+        out = torch.empty(blocks * thr, dtype=torch.float64 if kind != 3 else torch.float32,
+                          device=dev)
+        op = ctypes.c_void_p(out.data_ptr())
+        iters = 64
+        for _ in range(2):
+            st = lib.eig3_peak_loop(kind, chains, blocks, thr, iters, op, sp)
+            if st != 0:
+                raise RuntimeError(f"eig3_peak_loop failed with CUDA error {st}")
+        ms = timed(lambda: lib.eig3_peak_loop(kind, chains, blocks, thr, iters, op, sp), 1, stream)
+        iters = max(64, int(iters * target_ms / max(ms, 1e-3)))
+        ms = timed(lambda: lib.eig3_peak_loop(kind, chains, blocks, thr, iters, op, sp), 1, stream)
+        rate = blocks * thr * iters * chains / (ms * 1e-3) / 1e12
+        runs.append({"kind": kind, "chains": chains, "blocks_per_sm": bps, "threads": thr,
+                     "ms": ms, "T_inst_per_s": rate})
+        return rate
+
+    with ClockSampler(dev.index or 0) as clocks:
+        fp64 = max(one(kind, c, b, 256, 30.0) for kind in (0, 4, 5) for c in (2, 8)
+                   for b in (1, 4))
+        fp32 = max(one(3, c, b, 256, 30.0) for c in (8, 16) for b in (4, 8))
+    return {"fp64_tinst_per_s": fp64, "fp64_tflops_measured": 2.0 * fp64,
+            "fp32_tinst_per_s": fp32, "fp32_tflops_measured": 2.0 * fp32,
+            "fp64_loops": "DFMA chains alone and between integer or FFMA work, "
+                          "2 or 8 chains per thread, 1 or 4 blocks of 256 per SM; best",
+            "clocks": clocks.summary(), "runs": runs}
+
+
+def kernel_roofline(name, label, n, ms, fp, sm_mhz, sms, hbm_gbs):
+    """Roofline object of one binary64 kernel launch: the flop basis (counted
+    FP operations, FMA = 2, from its ncu counters) against the measured FP64
+    peak, with the FP64-pipe issue view and the nominal unit-count peak
+    beside it.  Null where the counters are stale."""
+    c = KERNEL_COUNTERS[name]
+    fresh = c["source_md5"] is not None and kernel_source_md5(KERNEL_SOURCES[name]) == c[
+        "source_md5"]
+    t = ms * 1e-3
+    nominal_inst = sms * FP64_LANES_PER_SM * sm_mhz * 1e6 / 1e12         # T inst/s
+    peak = fp["fp64_tflops_measured"]
+    out = {"kernel": label, "bound": "alu", "unit": "TFLOP/s", "counters_fresh": fresh,
+           "peak": peak,
+           "peak_source": f"measured in this run: fastest DFMA loop (libeig3_peaks), "
+                          f"{fp['fp64_tinst_per_s']:.4f} T DFMA/s",
+           "peak_nominal": 2.0 * nominal_inst,
+           "peak_nominal_source": f"{sms} SMs x {FP64_LANES_PER_SM} FP64 FMA lanes x "
+                                  f"{sm_mhz:.0f} MHz x 2 flop",
+           "fp64_tflops_measured": fp["fp64_tflops_measured"],
+           "fp32_tflops_measured": fp["fp32_tflops_measured"],
+           "ms": ms, "matrices": n, "G_matrices_per_s": n / t / 1e9}
+    hbm = KERNEL_BYTES[name]
+    out["hbm_view"] = {"bytes_per_matrix": hbm, "achieved_gbs": hbm * n / t / 1e9,
+                       "peak_gbs": hbm_gbs, "frac": hbm * n / t / 1e9 / hbm_gbs}
+    if not fresh:
+        out.update(achieved=None, frac=None, frac_vs_nominal=None, frac_issue=None, traffic=None)
+        return out
+    flop = 2 * c["dfma"] + c["dmul"] + c["dadd"]
+    achieved = flop * n / t / 1e12
+    inst_rate = c["fp64_warp_inst_x32"] * n / t / 1e12      # pipe occupancy
+    out.update(achieved=achieved, frac=achieved / peak,
+               frac_vs_nominal=achieved / (2.0 * nominal_inst),
+               frac_issue=inst_rate / nominal_inst,
+               frac_issue_vs_measured_loop=inst_rate / fp["fp64_tinst_per_s"],
+               traffic=c["dram_bytes"] * n,
+               algorithmic_per_matrix={"flop": flop, "fp64_pipe_inst": c["fp64_pipe_inst"],
+                                       "fp64_warp_inst_x32": c["fp64_warp_inst_x32"],
+                                       "dfma": c["dfma"], "dmul": c["dmul"], "dadd": c["dadd"],
+                                       "hbm_bytes": hbm},
+               mix_ceiling=flop / (2.0 * c["fp64_warp_inst_x32"]))
+    return out
+
+
+def self_launch_command(gpus: int, argv) -> list:
+    """The torchrun command that `bench.py --gpus N` (N > 1, outside torchrun)
+    re-executes itself under: one rank per GPU of this node, rendezvous on
+    127.0.0.1 at a free port."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={gpus}", "--master-addr=127.0.0.1", f"--master-port={port}",
+            os.path.abspath(__file__), *argv]
+
+
 def run_ours(args):
     import paper_2511_00292_gb300 as eig3
     from paper_2511_00292_gb300 import build as _b
@@ -333,47 +478,35 @@ def run_ours(args):
     S, G = w5["sym6"], w5["general9"]
     nS, nG = S.n, G.n
     lamS = torch.empty(nS, 3, dtype=torch.float32, device=dev)
-    auxS = torch.empty(nS, 4, dtype=torch.float32, device=dev)
     gS = torch.empty_like(S.A)
     lamG = torch.empty(nG, 3, dtype=torch.float64, device=dev)
-    auxG = torch.empty(nG, 4, dtype=torch.float64, device=dev)
     gG = torch.empty_like(G.A)
     wS, wG = S.extra["w"], G.extra["w"]
     stats = eig3.Stats(dev)
 
-    def fwd_S():
-        eig3.eigvals(S.A, precision="f32c", return_aux=True, out=lamS, aux_out=auxS, stats=stats)
+    # One step: eigenvalues and the gradient of sum(w * lambda) for both halves,
+    # each in one fused launch (eig3_eigvals_vjp).  The binary64 kernel keeps the
+    # FP64 pipe busy with little else; the compensated binary32 kernel uses the
+    # FP32 pipes, so it runs on a second stream beside it.
+    def vjp_S():
+        eig3.eigvals_vjp(S.A, wS, precision="f32c", out=lamS, grad_out=gS, stats=stats)
 
-    def bwd_S():
-        eig3.eigvals_backward(S.A, wS, aux=auxS, precision="f32c", out=gS)
+    def vjp_G():
+        eig3.eigvals_vjp(G.A, wG, precision="f64", out=lamG, grad_out=gG, stats=stats)
 
-    def fwd_G():
-        eig3.eigvals(G.A, precision="f64", return_aux=True, out=lamG, aux_out=auxG, stats=stats)
-
-    def bwd_G():
-        eig3.eigvals_backward(G.A, wG, aux=auxG, precision="f64", out=gG)
-
-    # The two halves are independent.  The binary64 kernels keep the FP64 pipe
-    # busy with little else; the compensated binary32 kernels use the FP32
-    # pipes, so they run on a second stream beside them.  Launched eagerly (4
-    # launches per step): replaying the same work as one CUDA graph measured
-    # 70.8-72.6 ms per step from run to run, the eager launches a steady 70.6 ms
-    # (the graph does not keep the binary64 kernels' blocks first on the SMs).
     s64, s32 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
     def step():
         s64.wait_stream(stream)
         s32.wait_stream(stream)
         with torch.cuda.stream(s64):
-            fwd_G()
-            bwd_G()
+            vjp_G()
         with torch.cuda.stream(s32):
-            fwd_S()
-            bwd_S()
+            vjp_S()
         stream.wait_stream(s64)
         stream.wait_stream(s32)
 
-    launches_per_step = 4
+    launches_per_step = 2
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize(dev)
@@ -393,49 +526,49 @@ def run_ours(args):
     barrier()
     ms = max_over_ranks(ms, dev)
     value = weak_scaling_value(world, N_MIXED, ms)
+    step_stats = stats.read()
 
-    # ---- per-kernel durations (eager, same launches, events on the launch stream) ----
+    # ---- per-kernel durations (each launch alone, events on the launch stream) ----
+    lamG4 = torch.empty(nG, 4, dtype=torch.float64, device=dev)
+
+    def fwd_G():
+        eig3.eigvals(G.A, precision="f64", return_aux=True, out=lamG, aux_out=lamG4, stats=stats)
+
     kern = {}
-    for name, fn in (("fwd_f32c_sym6", fwd_S), ("bwd_f32c_sym6", bwd_S),
-                     ("fwd_f64_general9", fwd_G), ("bwd_f64_general9", bwd_G)):
+    for name, fn in (("vjp_f32c_sym6", vjp_S), ("vjp_f64_general9", vjp_G),
+                     ("fwd_f64_general9", fwd_G)):
         fn()
         kern[name] = timed(fn, args.steps, stream)
+    del lamG4
+    fp = measure_fp_peaks(dev, stream)
     pk, pk_src = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    sm_mhz = clocks.summary().get("sm_mhz") or float(pk.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_inst = sms * FP64_LANES_PER_SM * sm_max * 1e6 / 1e12      # T inst/s
-    c = FWD_F64_COUNTERS
-    fresh = kernel_source_md5(FWD_F64_SOURCES) == c["source_md5"]
-    t_fwdG = kern["fwd_f64_general9"] * 1e-3
-    achieved = c["fp64_pipe_inst"] * nG / t_fwdG / 1e12
-    flop = 2 * c["dfma"] + c["dmul"] + c["dadd"]
-    roofline = {"kernel": "k_eigvals<general9, f64, aux, stats> (binary64 forward, 2^27 matrices)",
-                "bound": "alu", "unit": "T FP64-pipe inst/s", "achieved": achieved,
-                "peak": peak_inst, "frac": achieved / peak_inst,
-                "traffic": c["dram_bytes"] * nG if fresh else None,
-                "counters_fresh": fresh,
-                "peak_source": f"{sms} SMs x {FP64_LANES_PER_SM} FP64 lanes x {sm_max:.0f} MHz "
-                               f"(unit counts and clock; MEASURED_PEAKS has no FP64 figure)",
-                "algorithmic_per_matrix": {"fp64_pipe_inst": c["fp64_pipe_inst"], "dfma": c["dfma"],
-                                           "dmul": c["dmul"], "dadd": c["dadd"],
-                                           "hbm_bytes": 72 + 24 + 32},
-                "flop_view": {"achieved_tflops": flop * nG / t_fwdG / 1e12,
-                              "peak_tflops": 2 * peak_inst, "frac": flop * nG / t_fwdG / 1e12 /
-                              (2 * peak_inst)},
-                "hbm_view": {"achieved_gbs": (72 + 24 + 32) * nG / t_fwdG / 1e9,
-                             "peak_gbs": pk.get("hbm_gbs"), "peak_source": pk_src,
-                             "datasheet_gbs": 7900.0},
-                "kernel_ms": kern}
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    roofline = kernel_roofline(
+        "vjp_f64_general9", "k_eigvals_vjp<general9, f64> (fused forward + vector-Jacobian "
+        "product, binary64; the step's dominant launch, 2^27 matrices)", nG,
+        kern["vjp_f64_general9"], fp, sm_mhz, sms, hbm)
+    roofline["hbm_view"]["peak_source"] = pk_src
+    roofline["kernel_ms"] = kern
+    roofline_fwd = kernel_roofline(
+        "fwd_f64_general9", "k_eigvals<general9, f64, aux, stats> (binary64 forward, "
+        "2^27 matrices)", nG, kern["fwd_f64_general9"], fp, sm_mhz, sms, hbm)
+    ops = ORACLE_OPS_EIGVALS_GENERAL9
+    lit = ops["add"] + ops["mul"] + ops["div"]
+    roofline_fwd["oracle_literal_ops_per_matrix"] = dict(ops, flop=lit)
+    roofline_fwd["frac_oracle_literal_flop"] = lit * nG / (kern["fwd_f64_general9"] * 1e-3) / 1e12 \
+        / fp["fp64_tflops_measured"]
 
     # ---- the other workloads' paths (fwd, fwd+bwd, FP64 vs compensated FP32) ----
     paths = {}
     if not args.skip_paths:
-        paths = measure_paths(eig3, W, dev, stream, args.steps)
+        paths = measure_paths(eig3, W, dev, stream, args.steps, S=S, G=G, step_fns=dict(
+            vjp_S=vjp_S, vjp_G=vjp_G, s64=s64, s32=s32), lam=(lamS, lamG), grad=(gS, gG))
 
     # ---- end to end through host buffers (pinned), public API ----
     e2e = None
     if not args.skip_e2e:
-        # page-locked host buffers per rank: inputs and outputs of both halves
         per_rank = (S.A.numel() * 4 + nS * 12) * 2 + (G.A.numel() * 8 + nG * 24) * 2 + (1 << 30)
         shift = e2e_shift(world, per_rank, host_available_bytes())
         barrier()
@@ -452,16 +585,16 @@ def run_ours(args):
            "dtype": "f64+f32c", "data": "synthetic",
            "config": {"workload": WORKLOAD, "matrices_per_gpu": N_MIXED,
                       "l2": "inputs ~18 GB/step > 129 MB L2, no flush needed",
-                      "launch": "4 kernels per step, the binary32 pair on a second stream "
-                                "beside the binary64 pair"},
-           "roofline": roofline, "gpu_launches": launches_per_step * args.steps,
-           "clocks": clocks.summary(), "e2e": e2e, "paths": paths,
-           "stats": stats.read()}
+                      "launch": "2 kernels per step (eig3_eigvals_vjp for each half), the "
+                                "binary32 one on a second stream beside the binary64 one"},
+           "roofline": roofline, "roofline_fwd": roofline_fwd, "fp_peaks": fp,
+           "gpu_launches": launches_per_step * args.steps,
+           "clocks": clocks.summary(), "e2e": e2e, "paths": paths, "stats": step_stats}
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) ----
     if rank == 0 and world == 1 and not args.skip_cpu:
-        out["cpu_baseline"], out["max_err_over_bound"] = cpu_baseline(
-            eig3, S, G, lamS, lamG, gS, gG)
+        out["cpu_baseline"], out["max_err_over_bound"], out["err_vs_exact"] = cpu_baseline(
+            eig3, W, dev, S, G, lamS, lamG)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -469,9 +602,66 @@ def run_ours(args):
     return 0
 
 
-def measure_paths(eig3, W, dev, stream, steps):
+def measure_paths(eig3, W, dev, stream, steps, S, G, step_fns, lam, grad):
     paths = {}
     steps = max(steps, 3)
+    vjp_S, vjp_G, s64, s32 = (step_fns[k] for k in ("vjp_S", "vjp_G", "s64", "s32"))
+
+    def step_on(base):
+        s64.wait_stream(base)
+        s32.wait_stream(base)
+        with torch.cuda.stream(s64):
+            vjp_G()
+        with torch.cuda.stream(s32):
+            vjp_S()
+        base.wait_stream(s64)
+        base.wait_stream(s32)
+
+    # the benchmark step in the literal form of workload 5: 10 forward + backward
+    # steps captured once as one CUDA graph and replayed
+    step_on(stream)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cap = torch.cuda.current_stream(dev)
+        for _ in range(10):
+            step_on(cap)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    reps = max(1, steps // 10 + 1)
+    tg = timed(graph.replay, reps, stream) / 10
+    paths["mixed_step_graph_10_steps"] = {
+        "ms_per_step": tg, "G_matrices_per_s": (S.n + G.n) / tg / 1e6,
+        "form": "10 fused fwd+bwd steps captured once in a CUDA graph (20 kernel nodes on two "
+                "streams), replayed"}
+    del graph
+    # the same step unfused (eig3_eigvals with adjoint inputs, then
+    # eig3_eigvals_backward, for each half), as the autograd path runs it
+    lamS, lamG = lam
+    gS, gG = grad
+    auxS = torch.empty(S.n, 4, dtype=torch.float32, device=dev)
+    auxG = torch.empty(G.n, 4, dtype=torch.float64, device=dev)
+    wS, wG = S.extra["w"], G.extra["w"]
+
+    def unfused():
+        s64.wait_stream(stream)
+        s32.wait_stream(stream)
+        with torch.cuda.stream(s64):
+            eig3.eigvals(G.A, return_aux=True, out=lamG, aux_out=auxG)
+            eig3.eigvals_backward(G.A, wG, aux=auxG, out=gG)
+        with torch.cuda.stream(s32):
+            eig3.eigvals(S.A, precision="f32c", return_aux=True, out=lamS, aux_out=auxS)
+            eig3.eigvals_backward(S.A, wS, aux=auxS, precision="f32c", out=gS)
+        stream.wait_stream(s64)
+        stream.wait_stream(s32)
+
+    unfused()
+    tu = timed(unfused, steps, stream)
+    paths["mixed_step_unfused"] = {"ms_per_step": tu, "G_matrices_per_s": (S.n + G.n) / tu / 1e6,
+                                   "form": "eig3_eigvals + eig3_eigvals_backward per half, "
+                                           "4 launches on two streams"}
+    del auxS, auxG
+    torch.cuda.empty_cache()
     b2 = W.workload2(n=1 << 26, device=dev)
     lam = torch.empty(b2.n, 3, dtype=torch.float64, device=dev)
     t = timed(lambda: eig3.eigvals(b2.A, out=lam), steps, stream)
@@ -499,6 +689,8 @@ def measure_paths(eig3, W, dev, stream, steps):
 
     t4 = timed(fb, steps, stream)
     paths["fwd_bwd_f64_general9_2^24"] = {"G_matrices_per_s": b4.n / t4 / 1e6, "ms": t4}
+    t4v = timed(lambda: eig3.eigvals_vjp(b4.A, w4, out=lam4, grad_out=g4), steps, stream)
+    paths["vjp_f64_general9_2^24"] = {"G_matrices_per_s": b4.n / t4v / 1e6, "ms": t4v}
     P4 = torch.empty(b4.n, 27, dtype=torch.float64, device=dev)
     tp = timed(lambda: eig3.eigprojectors(b4.A, out=P4, return_eigvals=True, lam_out=lam4),
                steps, stream)
@@ -594,7 +786,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0):
 
     step()
     torch.cuda.synchronize(dev)
-    k = max(1, min(steps, 3))
+    k = max(1, steps)
     ms = timed(step, k, stream)
     # the copy ceiling on this machine: the same pinned buffers, 1 GiB each way
     # at once (host-to-device on one stream, device-to-host on another)
@@ -634,12 +826,84 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0):
                               "frac": floor_ms / ms}}
 
 
-def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
+def ratio_stats(err, bound):
+    """max and p99.9 of err / bound over the finite rows (0/0 counts as 0)."""
+    err = np.asarray(err, dtype=np.float64)
+    bound = np.asarray(bound, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(err == 0, 0.0, err / bound)
+    r = r[np.isfinite(err)]
+    if r.size == 0:
+        return {"max": None, "p999": None}
+    return {"max": float(np.max(r)), "p999": float(np.quantile(r, 0.999))}
+
+
+def err_vs_exact(eig3, W, dev, S, G, lamS, lamG, k=1 << 13):
+    """Distance of the GPU results from the exact values of the stored matrices
+    (oracle.eigvals_exact / invariants_exact, rational and 60-digit
+    arithmetic), per eigenvalue and per invariant, in units of the paper's
+    first-order bounds at C = 1 (Lemma of Section "Eigenvalues": kappa
+    ||A||_F u; Sections I1, J2, J3, Delta for the invariants), with u = 2^-53
+    for the binary64 path and 2^-24 for the compensated binary32 one.
+    Samples of k matrices per workload (all 4160 of workload 1), both halves
+    of the benchmark step from the step's own eigenvalues."""
+    import oracle
+    procs = os.cpu_count() or 1
+    U64, U32 = 2.0 ** -53, 2.0 ** -24
+    sets = []
+    A1 = W.workload1("cpu")["general9"].A
+    d1 = A1.to(dev)
+    sets.append(("workload1_general9_f64", A1.numpy(), 0, np.ones(A1.shape[0]), eig3.eigvals(d1),
+                 eig3.invariants(d1), U64))
+    b2 = W.workload2(n=k, device="cpu", seed=1202)
+    d2 = b2.A.to(dev)
+    sets.append(("workload2_general9_f64", b2.A.numpy(), 0, b2.kappa.numpy(), eig3.eigvals(d2),
+                 eig3.invariants(d2), U64))
+    b3 = W.workload3(n=k, device="cpu", seed=1203)
+    d3 = b3.A.to(dev)
+    sets.append(("workload3_sym6_f32c", b3.A.double().numpy(), 1, np.ones(k),
+                 eig3.eigvals(d3, precision="f32c"), eig3.invariants(d3, precision="f32c"), U32))
+    b4 = W.workload4(n=k, device="cpu", seed=1204)
+    d4 = b4.A.to(dev)
+    lam4, _ = eig3.eigvals_vjp(d4, b4.extra["w"].to(dev))
+    sets.append(("workload4_general9_f64_vjp", b4.A.numpy(), 0, b4.kappa.numpy(), lam4,
+                 eig3.invariants(d4), U64))
+    iS = torch.as_tensor(W.sample_indices(S.n, k, seed=13), device=S.A.device)
+    iG = torch.as_tensor(W.sample_indices(G.n, k, seed=14), device=G.A.device)
+    sets.append(("workload5_sym6_f32c_half", S.A[iS].double().cpu().numpy(), 1, np.ones(k),
+                 lamS[iS], eig3.invariants(S.A[iS].contiguous(), precision="f32c"), U32))
+    sets.append(("workload5_general9_f64_half", G.A[iG].cpu().numpy(), 0, G.kappa[iG].cpu().numpy(),
+                 lamG[iG], eig3.invariants(G.A[iG].contiguous()), U64))
+    out = {"bound": "C = 1: kappa ||A||_F u for eigenvalues, the first-order bounds of Sections "
+                    "I1, J2, J3, Delta for the invariants; exact values of the stored matrices",
+           "sets": {}}
+    t0 = time.perf_counter()
+    for name, A, lay, kappa, lam, inv, u in sets:
+        lam_x = oracle.map_eigvals_exact(A, lay, procs)
+        inv_x = oracle.map_invariants_exact(A, lay, procs)
+        b = oracle.bounds(A, kappa, layout=lay, u=u)
+        lam_g = lam.double().cpu().numpy()
+        inv_g = inv.cpu().numpy()
+        real = np.all(np.isfinite(lam_x), axis=1)       # complex spectra of fl(A) are NaN
+        e = {"matrices": int(A.shape[0]), "real_spectra": int(real.sum())}
+        for j in range(3):
+            e[f"lambda{j + 1}"] = ratio_stats(np.abs(lam_g[real, j] - lam_x[real, j]),
+                                              b[real, 4])
+        for j, nm in enumerate(("I1", "J2", "J3", "Delta")):
+            e[nm] = ratio_stats(np.abs(inv_g[:, j] - inv_x[:, j]), b[:, j])
+        out["sets"][name] = e
+    out["cpu_seconds"] = time.perf_counter() - t0
+    out["processes"] = procs
+    return out
+
+
+def cpu_baseline(eig3, W, dev, S, G, lamS, lamG):
     """The FP64 oracle (as it stands) on the host cores, on a bounded sample of
     the workload; the same sample gives the max error over the stability bound
-    of the GPU results."""
+    of the GPU results against the oracle.  Also workload 1 timed whole (the
+    oracle's forward in ms) and the distance of the GPU results from the exact
+    eigenvalues and invariants (err_vs_exact)."""
     import oracle
-    import workloads as W
     oracle.build()
     threads = os.cpu_count() or 1
     k = 1 << 24  # 2 x 2^24 matrices: about 12 s of CPU time on 16 Grace cores
@@ -658,7 +922,18 @@ def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
     t1 = time.perf_counter()
     oracle_step(oracle, S64[:m], G64[:m], wS[:m], wG[:m], 1)
     ns_1t = (time.perf_counter() - t1) / (2 * m) * 1e9
-    # accuracy of the GPU results on this sample
+    # workload 1 whole (4096 + 64 symmetric matrices, general 9-entry storage):
+    # the oracle's forward, one thread and all threads, best of 3
+    A1 = W.workload1("cpu")["general9"].A.numpy()
+    t_1, t_all = [], []
+    for _ in range(3):
+        t = time.perf_counter()
+        oracle.eigvals(A1)
+        t_1.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        oracle.eigvals_mt(A1, nthreads=threads)
+        t_all.append(time.perf_counter() - t)
+    # accuracy of the GPU results on this sample, against the oracle
     refS = np.sort(refS, axis=1)
     refG = np.sort(refG, axis=1)
     bS = oracle.bounds(S64, 1.0, layout=oracle.SYM6, u=2.0 ** -24)[:, 4]
@@ -670,16 +945,21 @@ def cpu_baseline(eig3, S, G, lamS, lamG, gS, gG):
                      f"mixed workload, eigenvalues + eigenvector-form gradient, "
                      f"{dt:.2f} s wall on {threads} threads "
                      f"(about {dt * threads:.0f} s of CPU time)",
-           "single_thread_ns_per_matrix": ns_1t}
+           "single_thread_ns_per_matrix": ns_1t,
+           "workload1_forward_ms": {"matrices": int(A1.shape[0]), "one_thread": 1e3 * min(t_1),
+                                    "all_threads": 1e3 * min(t_all), "threads": threads}}
     err = {"f32c_sym6": float(np.max(eS / bS)), "f64_general9": float(np.max(eG / bG)),
-           "bound": "kappa ||A||_F u (u = 2^-24 for f32c, 2^-53 for f64; C = 1)",
+           "f32c_sym6_p999": float(np.quantile(eS / bS, 0.999)),
+           "f64_general9_p999": float(np.quantile(eG / bG, 0.999)),
+           "bound": "kappa ||A||_F u (u = 2^-24 for f32c, 2^-53 for f64; C = 1), GPU against "
+                    "the oracle",
            "sample_matrices": int(S64.shape[0] + G64.shape[0])}
-    return cpu, err
+    return cpu, err, err_vs_exact(eig3, W, dev, S, G, lamS, lamG)
 
 
 KERNELS = ("fwd_f64_general9", "bwd_f64_general9", "fwd_f32c_sym6", "bwd_f32c_sym6",
            "fwd_f64_sym6", "mc_f64_sym6", "mc_f32c_sym6", "guard_f64_illcond",
-           "proj_f32c_sym6")
+           "proj_f32c_sym6", "vjp_f64_general9", "vjp_f32c_sym6")
 
 
 def run_single(args):
@@ -730,6 +1010,8 @@ def run_single(args):
     if args.only.startswith("fwd"):
         fn = lambda: eig3.eigvals(A, precision=prec, return_aux=True, out=lam, aux_out=aux,
                                   stats=st)
+    elif args.only.startswith("vjp"):
+        fn = lambda: eig3.eigvals_vjp(A, w, precision=prec, out=lam, grad_out=g, stats=st)
     else:
         fn = lambda: eig3.eigvals_backward(A, w, aux=aux, precision=prec, out=g)
     for _ in range(args.warmup):
@@ -751,9 +1033,22 @@ def main():
     ap.add_argument("--only", choices=KERNELS, default=None,
                     help="time one kernel alone at size --n (profiler captures)")
     ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 / FP32 pipe peaks only and print them")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: re-run this command under torchrun
+        return subprocess.call(self_launch_command(args.gpus, sys.argv[1:]))
     if args.impl == "reference":
         return run_reference(args)
+    if args.peaks:
+        from paper_2511_00292_gb300 import build as _b
+        _b.build()
+        dev = torch.device("cuda", env_int("LOCAL_RANK", 0))
+        torch.cuda.set_device(dev)
+        fp = measure_fp_peaks(dev, torch.cuda.current_stream(dev))
+        print(json.dumps(fp), flush=True)
+        return 0
     if args.only:
         return run_single(args)
     return run_ours(args)

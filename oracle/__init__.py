@@ -23,6 +23,10 @@ Function map (paper sections):
     eigvals_exact     (oracle/exact.py) the exact eigenvalues of the stored
                       matrix: roots of its exact characteristic polynomial,
                       the reference the stability bounds are stated against
+    invariants_exact  (oracle/exact.py) the exact invariants of the stored matrix
+    opcount           the operations of one oracle function on one matrix,
+                      counted by compiling eig3_oracle.c with an op-counting
+                      scalar type (opcount.cpp, g++)
 """
 from __future__ import annotations
 
@@ -37,6 +41,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "eig3_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libeig3_oracle.so")
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_BUILD, "libeig3_opcount.so")
 
 GENERAL9 = 0
 SYM6 = 1
@@ -57,6 +63,19 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def _build_opcount() -> str:
+    """Compile opcount.cpp (the oracle's source with a counting scalar) with g++."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_OPC_SRC))
+    if not os.path.exists(_OPC_LIB) or os.path.getmtime(_OPC_LIB) < newest:
+        tmp = _OPC_LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-std=c++17", "-I", _HERE, "-o", tmp, _OPC_SRC, "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OPC_LIB)
+    return _OPC_LIB
 
 
 def _load():
@@ -204,6 +223,36 @@ def eigvals_mt(X, layout: int = GENERAL9, nthreads: int | None = None):
     return out, int(used)
 
 
+_OPC = {"eigvals": 0, "invariants": 1, "I1": 2, "J2": 3, "J3": 4, "Delta": 5,
+        "eigvals_from_invariants": 6}
+_OPC_FIELDS = ("add", "mul", "div", "neg", "sqrt", "atan2", "cos", "cmp", "abs")
+_opc_lib = None
+
+
+def opcount(function: str, a) -> tuple[dict, np.ndarray]:
+    """(counts, results) of one oracle function on one general 9-entry matrix
+    (for "eigvals_from_invariants": the four invariants), from the oracle's
+    source compiled with an op-counting scalar type.  counts maps each kind of
+    operation (add includes subtraction) to how many the function performed."""
+    global _opc_lib
+    with _lock:
+        if _opc_lib is None:
+            lib = ctypes.CDLL(_build_opcount())
+            lib.eig3o_opcount.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]
+            lib.eig3o_opcount.restype = ctypes.c_int
+            _opc_lib = lib
+    x = np.zeros(9)
+    v = np.asarray(a, dtype=np.float64).reshape(-1)
+    x[:v.size] = v
+    counts = np.zeros(9, dtype=np.int64)
+    res = np.full(4, np.nan)
+    if _opc_lib.eig3o_opcount(_OPC[function], _ptr(x), _ptr(counts), _ptr(res)) != 0:
+        raise ValueError(function)
+    n = {"eigvals": 3, "invariants": 4, "eigvals_from_invariants": 3}.get(function, 1)
+    return dict(zip(_OPC_FIELDS, (int(c) for c in counts))), res[:n]
+
+
 def sym6_to_general9(S) -> np.ndarray:
     """Expand (A00, A11, A22, A12, A02, A01) rows to row-major 9-entry rows."""
     S = np.asarray(S, dtype=np.float64).reshape(-1, 6)
@@ -214,4 +263,5 @@ def sym6_to_general9(S) -> np.ndarray:
     return A
 
 
-from .exact import eigvals_exact  # noqa: E402  (pure Python, no compiled part)
+from .exact import (eigvals_exact, invariants_exact, map_eigvals_exact,  # noqa: E402
+                    map_invariants_exact)  # (pure Python, no compiled part)

@@ -21,11 +21,25 @@ is found by bisection in decimal arithmetic with 60 significant digits
 This is the reference the stability bounds of the paper are stated against
 (the exact eigenvalues of fl(A)); it is slow (milliseconds per matrix) and
 meant for samples of a few thousand matrices.
+
+invariants_exact gives the exact invariants of fl(A) from the same exact
+coefficients: with I1 = -c2, I2 = c1 and I3 = -c0 (trace, sum of the
+principal minors, determinant),
+
+    J2 = I1^2/3 - I2,   J3 = 2 I1^3/27 - I1 I2/3 + I3,   Delta = 4 J2^3 - 27 J3^2,
+
+the invariants of the deviator S = A - (I1/3) I (J2 = tr(S^2)/2 and
+J3 = det S, since S has the characteristic polynomial of A shifted by I1/3),
+each rounded once to binary64.  The map_* helpers spread either over worker
+processes started with spawn (safe beside a CUDA context).
 """
 from __future__ import annotations
 
 from decimal import Decimal, localcontext
 from fractions import Fraction
+
+import multiprocessing as mp
+from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 
@@ -131,3 +145,50 @@ def eigvals_exact(X, layout: int = 0) -> np.ndarray:
             r = _roots(*charpoly(a))
             out[i] = np.nan if r is None else [float(x) for x in r]
     return out
+
+
+def _general9(X, layout: int) -> np.ndarray:
+    X = np.asarray(X, dtype=np.float64)
+    if layout == 1:
+        S = X.reshape(-1, 6)
+        X = np.stack([S[:, 0], S[:, 5], S[:, 4], S[:, 5], S[:, 1], S[:, 3],
+                      S[:, 4], S[:, 3], S[:, 2]], axis=1)
+    return X.reshape(-1, 9)
+
+
+def invariants_exact(X, layout: int = 0) -> np.ndarray:
+    """(n, 4) exact (I1, J2, J3, Delta) of the stored matrices, each rounded
+    once to binary64 (NaN rows for non-finite input)."""
+    X = _general9(X, layout)
+    out = np.empty((X.shape[0], 4))
+    for i, a in enumerate(X):
+        if not np.all(np.isfinite(a)):
+            out[i] = np.nan
+            continue
+        c2, c1, c0 = charpoly(a)
+        I1, I2, I3 = -c2, c1, -c0
+        J2 = I1 * I1 / 3 - I2
+        J3 = 2 * I1 ** 3 / 27 - I1 * I2 / 3 + I3
+        out[i] = [float(I1), float(J2), float(J3), float(4 * J2 ** 3 - 27 * J3 ** 2)]
+    return out
+
+
+def _chunked(fn, X, layout: int, processes: int) -> np.ndarray:
+    X = _general9(X, layout)
+    k = max(1, int(processes))
+    if k == 1 or X.shape[0] < 64:
+        return fn(X, 0)
+    parts = np.array_split(X, 4 * k)
+    with ProcessPoolExecutor(max_workers=k, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(fn, parts, [0] * len(parts)))
+    return np.concatenate(res, axis=0)
+
+
+def map_eigvals_exact(X, layout: int = 0, processes: int = 1) -> np.ndarray:
+    """eigvals_exact over `processes` spawned worker processes."""
+    return _chunked(eigvals_exact, X, layout, processes)
+
+
+def map_invariants_exact(X, layout: int = 0, processes: int = 1) -> np.ndarray:
+    """invariants_exact over `processes` spawned worker processes."""
+    return _chunked(invariants_exact, X, layout, processes)

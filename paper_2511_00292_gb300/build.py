@@ -3,7 +3,10 @@
 The translation units are compiled in parallel with nvcc and linked into
 ``paper_2511_00292_gb300/_build/libeig3.so`` (static CUDA runtime, no torch
 dependency: the C ABI takes plain pointers).  ptxas resource usage of every
-kernel is kept next to the objects (``_build/ptxas_<unit>.txt``).
+kernel is kept next to the objects (``_build/ptxas_<unit>.txt``).  The
+throughput loops that give the benchmark its FP64 / FP32 peaks
+(``csrc/eig3_peaks.cu``) go into a library of their own,
+``_build/libeig3_peaks.so``, which the eig3 ABI does not include.
 """
 from __future__ import annotations
 
@@ -19,6 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libeig3.so")
+PEAKS_LIB = os.path.join(BUILD, "libeig3_peaks.so")
+PEAKS_UNIT = "eig3_peaks.cu"
 
 UNITS = ["eig3_api.cu", "eig3_f64.cu", "eig3_f32c.cu", "eig3_mohr_coulomb.cu", "eig3_variants.cu",
          "eig3_guard.cu"]
@@ -55,16 +60,19 @@ def _compile(unit: str) -> str:
 def build(force: bool = False) -> str:
     """Compile (if stale) and link libeig3.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    fresh = all(os.path.exists(p) and os.path.getmtime(p) >= _deps_mtime()
+                for p in (LIB, PEAKS_LIB))
+    if not force and fresh:
         return LIB
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(_compile, UNITS))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(max_workers=len(UNITS) + 1) as ex:
+        objs = list(ex.map(_compile, UNITS + [PEAKS_UNIT]))
+    for lib, parts in ((LIB, objs[:-1]), (PEAKS_LIB, objs[-1:])):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *parts]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -54,13 +54,16 @@ def test_peaks_measured_file_or_fallback(tmp_path, monkeypatch):
     assert src == "measured" and pk["hbm_gbs"] == 6782.1
 
 
-def test_source_hash_marks_counters_fresh_or_stale(tmp_path, monkeypatch):
+@pytest.mark.parametrize("name", sorted(bench.KERNEL_SOURCES))
+def test_source_hash_marks_counters_fresh_or_stale(tmp_path, monkeypatch, name):
     """The hash covers the headers whole and, in the .cu file that also holds
-    other kernels, only the forward kernel's and its launchers' definitions."""
+    other kernels, only the kernel's own, its launchers' and its helpers'
+    definitions."""
+    sources = bench.KERNEL_SOURCES[name]
     csrc = tmp_path / "paper_2511_00292_gb300" / "csrc"
     csrc.mkdir(parents=True)
     cu = None
-    for src in bench.FWD_F64_SOURCES:
+    for src in sources:
         if isinstance(src, str):
             (csrc / src).write_text(f"// {src}\n")
         else:
@@ -70,26 +73,107 @@ def test_source_hash_marks_counters_fresh_or_stale(tmp_path, monkeypatch):
             other = "\n\nint other_kernel(int y) {\n  return y + k_eigvals<0>(y);\n}\n"
             (csrc / cu).write_text("// unit" + body + other)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    h0 = bench.kernel_source_md5(bench.FWD_F64_SOURCES)
-    assert h0 == bench.kernel_source_md5(bench.FWD_F64_SOURCES)
+    h0 = bench.kernel_source_md5(sources)
+    assert h0 == bench.kernel_source_md5(sources)
     text = (csrc / cu).read_text()
     changed = text.replace("return y +", "return 2 * y +")
     assert changed != text
     (csrc / cu).write_text(changed)                                   # another kernel
-    assert bench.kernel_source_md5(bench.FWD_F64_SOURCES) == h0
-    (csrc / cu).write_text(text.replace("x + 1", "x + 2", 1))          # the forward kernel
-    assert bench.kernel_source_md5(bench.FWD_F64_SOURCES) != h0
+    assert bench.kernel_source_md5(sources) == h0
+    (csrc / cu).write_text(text.replace("x + 1", "x + 2", 1))          # this kernel
+    assert bench.kernel_source_md5(sources) != h0
     (csrc / cu).write_text(text)
-    (csrc / bench.FWD_F64_SOURCES[0]).write_text("// changed header\n")
-    assert bench.kernel_source_md5(bench.FWD_F64_SOURCES) != h0
+    (csrc / sources[0]).write_text("// changed header\n")
+    assert bench.kernel_source_md5(sources) != h0
 
 
-def test_stored_counters_describe_the_committed_source():
+def _strip_comments(text):
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    return re.sub(r"//[^\n]*", " ", text)
+
+
+def _file_level_names(text):
+    """Names of the functions and structs defined at file scope of `text`
+    (namespace braces do not count as scopes)."""
+    import re
+    text = _strip_comments(text)
+    depth, stack, scope = 0, [], [True] * len(text)
+    for i, ch in enumerate(text):
+        if ch == "{":
+            ns = re.search(r"namespace\s*\w*\s*$", text[max(0, i - 48):i]) is not None
+            stack.append(ns)
+            depth += 0 if ns else 1
+        elif ch == "}":
+            depth -= 0 if (stack.pop() if stack else False) else 1
+        scope[i] = depth == 0
+    names = set()
+    for m in re.finditer(r"\bstruct\s+(\w+)\s*\{", text):
+        if scope[m.start()]:
+            names.add(m.group(1))
+    for m in re.finditer(r"\b([A-Za-z_]\w*)\s*\(", text):
+        name = m.group(1)
+        if not scope[m.start()] or name.startswith("__") or name in ("if", "for", "while"):
+            continue
+        k, d = m.end() - 1, 0
+        for k in range(m.end() - 1, len(text)):   # the parameter list
+            d += text[k] == "("
+            d -= text[k] == ")"
+            if d == 0:
+                break
+        rest = text[k + 1:k + 64].lstrip()
+        if rest.startswith("{") or rest.startswith("const {"):
+            names.add(name)
+    return names
+
+
+@pytest.mark.parametrize("name", sorted(bench.KERNEL_SOURCES))
+def test_hashed_functions_cover_the_kernel_helpers(name):
+    """Every definition of eig3_f64.cu that the kernel or its launchers use
+    (directly or through each other) is in the hashed list, so an edit to a
+    helper (such as the adjoint-input store) marks the counters stale."""
+    import re
+    cu, funcs = [s for s in bench.KERNEL_SOURCES[name] if not isinstance(s, str)][0]
+    text = open(os.path.join(bench.ROOT, "paper_2511_00292_gb300", "csrc", cu)).read()
+    local = _file_level_names(text)
+    assert set(funcs) <= local, set(funcs) - local
+    seen, todo = set(funcs), list(funcs)
+    while todo:
+        f = todo.pop()
+        for d in bench._definitions(_strip_comments(text), f):
+            for used in set(re.findall(r"\b(\w+)\s*[<(]", d)) & local:
+                if used not in seen:
+                    seen.add(used)
+                    todo.append(used)
+    assert seen <= set(funcs), f"{name}: not hashed: {sorted(seen - set(funcs))}"
+
+
+@pytest.mark.parametrize("name", sorted(bench.KERNEL_COUNTERS))
+def test_stored_counters_describe_the_committed_source(name):
     """The per-matrix ncu counters in bench.py were taken on the kernel source
     as committed; a source change without a new capture reports them stale."""
-    assert bench.kernel_source_md5(bench.FWD_F64_SOURCES) == bench.FWD_F64_COUNTERS["source_md5"]
-    c = bench.FWD_F64_COUNTERS
+    c = bench.KERNEL_COUNTERS[name]
+    assert bench.kernel_source_md5(bench.KERNEL_SOURCES[name]) == c["source_md5"]
     assert c["fp64_pipe_inst"] >= c["dfma"] + c["dmul"] + c["dadd"]
+
+
+def test_self_launch_command():
+    """--gpus N outside torchrun re-runs the same command under
+    torch.distributed.run: one rank per GPU, rendezvous on 127.0.0.1."""
+    cmd = bench.self_launch_command(4, ["--gpus", "4", "--steps", "5"])
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "--nnodes=1" in cmd
+    assert "--master-addr=127.0.0.1" in cmd
+    port = int([a for a in cmd if a.startswith("--master-port=")][0].split("=")[1])
+    assert 0 < port < 65536
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "5"]
+    assert cmd[-5].endswith("bench.py")
+
+
+def test_ratio_stats():
+    r = bench.ratio_stats([0.0, 1.0, 2.0, float("nan")], [0.0, 2.0, 1.0, 1.0])
+    assert r["max"] == 2.0
+    assert bench.ratio_stats([], [])["max"] is None
 
 
 def test_whole_job_throughput():
