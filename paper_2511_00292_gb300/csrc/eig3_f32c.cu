@@ -1,12 +1,13 @@
 // eig3_f32c.cu -- compensated binary32 kernels (storage and arithmetic in
 // binary32, see eig3_f32c.cuh): invariants, eigenvalues (+ adjoint inputs,
 // + statistics), the adjoint, the fused forward + vector-Jacobian product and
-// the eigenprojectors, for both layouts.  One thread per matrix; the
-// eigenvalue and fused kernels' warps walk the batch in tiles of 32 rows each
-// (for_each_row_warp), the others' blocks in tiles of 256 rows (for_each_row /
-// for_each_tile), the inputs copied into shared memory asynchronously one tile
-// ahead (eig3_tile.cuh); the 16-byte adjoint-input rows move as one float4
-// each; outputs are stored directly, the projectors through shared memory.
+// the eigenprojectors, for both layouts.  One thread per matrix; blocks walk
+// the batch in tiles of 256 rows (for_each_row / for_each_tile: for these
+// issue-bound kernels the block tiles measured 3-9% faster than the warp
+// tiles of the binary64 kernels), the inputs copied into shared memory
+// asynchronously one tile ahead (eig3_tile.cuh); the 16-byte adjoint-input
+// rows move as one float4 each; outputs are stored directly, the projectors
+// through shared memory.
 #include <cstdint>
 
 #include "eig3_f32c.cuh"
@@ -38,14 +39,13 @@ struct WidthC {
   static constexpr int N = (LAYOUT == EIG3_GENERAL9) ? 9 : 6;
 };
 
-// EIG: invariants for the eigenvalue kernels (see disc_sym_rounded);
-// otherwise for the invariants output.
-template <int LAYOUT, int N, bool EIG = true>
+// The compensated invariants (the invariants output, accurate at u32^2).
+template <int LAYOUT, int N>
 __device__ __forceinline__ InvC invariants_c(const float (&a)[N]) {
   if constexpr (LAYOUT == EIG3_GENERAL9) {
     return invariants_general_c(a);
   } else {
-    return invariants_sym_c<EIG>(a[0], a[1], a[2], a[3], a[4], a[5]);
+    return invariants_sym_c(a[0], a[1], a[2], a[3], a[4], a[5]);
   }
 }
 
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     float a[N];
     load_f<N>(A, i, a);
-    invariants_out(invariants_c<LAYOUT, N, false>(a), inv + 4 * i);
+    invariants_out(invariants_c<LAYOUT, N>(a), inv + 4 * i);
   }
 }
 
@@ -70,16 +70,15 @@ __global__ void __launch_bounds__(kThreads)
     k_eigvals_c(const float *__restrict__ A, int64_t n, float *__restrict__ lam,
                 float *__restrict__ aux, eig3_stats *__restrict__ stats) {
   constexpr int N = WidthC<LAYOUT>::N;
-  __shared__ __align__(16) float sW[kThreads / 32][2][kWarpTile * N];
+  __shared__ __align__(16) float sA[2][kTile * N];
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
   const bool vaux = AUX && aligned16c(aux);
-  for_each_row_warp<N, float>(A, n, sW[threadIdx.x >> 5], [&](int64_t i, const float *row) {
+  for_each_row<N, float>(A, n, sA, [&](int64_t i, const float *row) {
     float a[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a[j] = row[j];
-    const InvC v = invariants_c<LAYOUT, N>(a);
-    const EigC e = eigvals_c<ANGLE64>(v);
+    const EigC e = eig_c<N, ANGLE64>(a);
     lam[3 * i + 0] = e.l1;
     lam[3 * i + 1] = e.l2;
     lam[3 * i + 2] = e.l3;
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(kThreads)
         s2 = __ldg(aux + 4 * i + 2);
       }
     } else {
-      const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+      const EigC e = eig_c<N>(a);
       r = e.r;
       s1 = e.sigma1;
       s2 = e.sigma2;
@@ -153,24 +152,24 @@ __global__ void __launch_bounds__(kThreads)
 // Fused forward + vector-Jacobian product (eig3_eigvals_vjp): lambda
 // (optional) and dL/dA for L = sum_k w_k lambda_k in one pass per matrix,
 // the adjoint from the forward's r and sigmas in registers.  Rows of A go
-// through the warp's shared-memory tiles; the weights are read directly.
+// through the block's shared-memory tiles; the weights are read directly.
 template <int LAYOUT, bool LAM, bool STATS>
 __global__ void __launch_bounds__(kThreads)
     k_eigvals_vjp_c(const float *__restrict__ A, const float *__restrict__ w, int64_t n,
                     float *__restrict__ lam, float *__restrict__ gA,
                     eig3_stats *__restrict__ stats) {
   constexpr int N = WidthC<LAYOUT>::N;
-  __shared__ __align__(16) float sW[kThreads / 32][2][kWarpTile * N];
+  __shared__ __align__(16) float sA[2][kTile * N];
   StatAcc acc;
   if constexpr (STATS) stat_init(acc);
-  for_each_row_warp<N, float>(A, n, sW[threadIdx.x >> 5], [&](int64_t i, const float *row) {
+  for_each_row<N, float>(A, n, sA, [&](int64_t i, const float *row) {
     float a[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a[j] = row[j];
     const float g1 = __ldg(w + 3 * i + 0);
     const float g2 = __ldg(w + 3 * i + 1);
     const float g3 = __ldg(w + 3 * i + 2);
-    const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+    const EigC e = eig_c<N>(a);
     if constexpr (LAM) {
       lam[3 * i + 0] = e.l1;
       lam[3 * i + 1] = e.l2;
@@ -231,7 +230,7 @@ __global__ void __launch_bounds__(kThreads)
           float a[N];
 #pragma unroll
           for (int j = 0; j < N; ++j) a[j] = tA[threadIdx.x * N + j];
-          const EigC e = eigvals_c(invariants_c<LAYOUT, N>(a));
+          const EigC e = eig_c<N>(a);
           if constexpr (LAM) {
             sL[3 * threadIdx.x + 0] = e.l1;
             sL[3 * threadIdx.x + 1] = e.l2;

@@ -256,6 +256,158 @@ __device__ __forceinline__ InvC invariants_sym_c(float a00, float a11, float a22
 }
 
 // ---------------------------------------------------------------------------
+// Sums of products on a fixed grid, for the eigenvalue kernels.
+//
+// The eigenvalues do not need the scaled 6 J2, 27 J3 and r_i of Algorithm 5
+// at the u32^2 relative accuracy of Sum2: 6 J2 enters through its binary32
+// rounding, and 27 J3 and the r_i through the angle, whose error is their
+// ABSOLUTE error over sqrt(x^2 + y^2) = sqrt(108 J2^3), at least 1/sqrt(2)
+// once the scaling puts the largest deviatoric datum in [1, 2) (so 6 J2 >= 1).
+// A sum whose terms are bounded by the scaling is therefore accumulated on a
+// fixed grid (the extraction of Rump, Ogita and Oishi, "Accurate
+// floating-point summation part I: faithful rounding", SIAM J. Sci. Comput.
+// 31 (2008)):
+//   B = bias + S,  bias = 1.5 * 2^K at least twice every partial sum |S|,
+// so B stays in [bias/2, 3 bias/2]; two successive B then differ exactly
+// (Sterbenz) and S = B - bias is exact.  Adding a product x y is one FMA into
+// B, the exact difference of the old and new B, and one FMA giving the
+// rounding residual x y - (B' - B) (|residual| <= ulp(B)/2, itself rounded
+// once), which goes into the binary32 low part C; the low parts of pair
+// operands enter C by FMA.  4 instructions for x y, 5 for a pair times a
+// value, 6 for a pair times a pair, against 11 for a TwoSum-based Sum2 step;
+// the error is a few units of u32 * ulp(bias) instead of u32^2 relative.
+// The bounds on |S| below take the largest scaled datum below 4: it lies in
+// [1, 2) except for data beyond 2^127, where the clamped scale leaves [2, 4).
+// ---------------------------------------------------------------------------
+struct Grid {
+  float B, C;
+};
+
+template <int K>
+struct GridBias {
+  static constexpr float value = 1.5f * (float)(1 << K);
+};
+
+template <int K>
+__device__ __forceinline__ Grid gstart(float x, float y) {
+  const float b = __fmaf_rn(x, y, GridBias<K>::value);
+  return {b, __fmaf_rn(x, y, __fsub_rn(GridBias<K>::value, b))};
+}
+
+template <int K>
+__device__ __forceinline__ Grid gstart(F2 x, float y) {
+  const Grid g = gstart<K>(x.h, y);
+  return {g.B, __fmaf_rn(x.l, y, g.C)};
+}
+
+template <int K>
+__device__ __forceinline__ Grid gstart(F2 x, F2 y) {
+  const Grid g = gstart<K>(x.h, y.h);
+  return {g.B, __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.l, g.C))};
+}
+
+__device__ __forceinline__ Grid gadd(Grid g, float x, float y) {
+  const float b = __fmaf_rn(x, y, g.B);
+  return {b, __fadd_rn(g.C, __fmaf_rn(x, y, __fsub_rn(g.B, b)))};
+}
+
+__device__ __forceinline__ Grid gadd(Grid g, F2 x, float y) {
+  const Grid t = gadd(g, x.h, y);
+  return {t.B, __fmaf_rn(x.l, y, t.C)};
+}
+
+__device__ __forceinline__ Grid gadd(Grid g, F2 x, F2 y) {
+  const Grid t = gadd(g, x.h, y.h);
+  return {t.B, __fmaf_rn(x.l, y.h, __fmaf_rn(x.h, y.l, t.C))};
+}
+
+// The sum, rounded to binary32: (B - bias) exactly, plus C.
+template <int K>
+__device__ __forceinline__ float gsum(Grid g) {
+  return __fadd_rn(__fsub_rn(g.B, GridBias<K>::value), g.C);
+}
+
+// The difference of two sums on the same grid, rounded to binary32: B - B' is
+// exact (both lie in [bias/2, 3 bias/2] on the grid of that binade).
+__device__ __forceinline__ float gdiff(Grid x, Grid y) {
+  return __fadd_rn(__fsub_rn(x.B, y.B), __fsub_rn(x.C, y.C));
+}
+
+// The scaled invariants rounded to binary32 (the eigenvalue kernels' input).
+struct InvR {
+  float I1, J2x6, J3x27, D;
+  int e;  // the scale exponent
+};
+
+// Symmetric invariants for the eigenvalue kernels: the terms of
+// invariants_sym_c, each sum on its grid (K = 9 for 6 J2 < 336 and for the
+// r_i, four terms below 64 each; K = 14 for 27 J3 < 7424), the differences
+// d_i and t_i and the trace still exact pairs.  Delta is the weighted sum of
+// the squares of the rounded r_i, non-negative terms with nothing left to
+// cancel (disc_sym_rounded).  -r12 takes the place of r12: only its square
+// enters.  With r2, r3, r4 from differences of r8 .. r13 the symmetric Delta
+// takes 7 sums of products instead of 10.
+__device__ __forceinline__ InvR invariants_sym_eig(float a00, float a11, float a22, float c0,
+                                                   float b0, float a0) {
+  const Diag g = diag_parts(a00, a11, a22);
+  InvR o;
+  o.I1 = round1(g.I1);
+  const int E = scale_exponent(g.d0.h, g.d1.h, g.d2.h, a0, b0, c0, 0.f, 0.f, 0.f);
+  o.e = E - 127;
+  const float sc = pow2_from_field(254 - E);
+  const F2 d0 = scale2(g.d0, sc), d1 = scale2(g.d1, sc), d2 = scale2(g.d2, sc);
+  const float a = __fmul_rn(a0, sc), b = __fmul_rn(b0, sc), c = __fmul_rn(c0, sc);
+  const F2 aa = two_prod(a, a), bb = two_prod(b, b), cc = two_prod(c, c);
+  const F2 ab = two_prod(a, b), ac = two_prod(a, c), bc = two_prod(b, c);
+  // Algorithm 2, times 6: (d0^2 + d1^2 + d2^2) + 6 (aa + bb + cc)
+  Grid j2 = gstart<9>(d0, d0);
+  j2 = gadd(j2, d1, d1);
+  j2 = gadd(j2, d2, d2);
+  j2 = gadd(j2, aa, 6.0f);
+  j2 = gadd(j2, bb, 6.0f);
+  j2 = gadd(j2, cc, 6.0f);
+  o.J2x6 = gsum<9>(j2);
+  // Algorithm 4, times 27: 54 abc + 9 (aa t1 + bb t2 + cc t3) - t1 t2 t3
+  const F2 t1 = pair(start(d1) + d2);
+  const F2 t2 = pair(start(d0) - d2);
+  const F2 t3 = pair(start(neg(d0)) - d1);
+  Grid j3 = gstart<14>(mul(ab, c), 54.0f);
+  j3 = gadd(j3, mul(aa, t1), 9.0f);
+  j3 = gadd(j3, mul(bb, t2), 9.0f);
+  j3 = gadd(j3, mul(cc, t3), 9.0f);
+  j3 = gadd(j3, neg(mul(t1, t2)), t3);
+  o.J3x27 = gsum<14>(j3);
+  // Algorithm 5: r8 .. r14 on their grids; r2, r3, r4 from the symmetric
+  // identities r2 = r8 - r9, r3 = r12 + r13, r4 = r11 - r10 (d0 - d1 = -d2,
+  // d0 + d2 = d1, d1 - d2 = d0 for the exact pairs), the grid states
+  // subtracting exactly (gdiff)
+  const F2 d0d1 = mul(d0, d1), d0d2 = mul(d0, d2), d1d2 = mul(d1, d2);
+  const Grid s89 = gadd(gstart<9>(d0d1, c), neg(cc), c);
+  const Grid g8 = gadd(gadd(s89, aa, c), neg(ab), d1);
+  const Grid g9 = gadd(gadd(s89, bb, c), neg(ab), d0);
+  const Grid s1011 = gadd(gstart<9>(d1d2, a), neg(aa), a);
+  const Grid g10 = gadd(gadd(s1011, bc, d2), bb, a);
+  const Grid g11 = gadd(gadd(s1011, bc, d1), cc, a);
+  const Grid s1213 = gadd(gstart<9>(d0d2, b), bb, b);
+  const Grid g13 = gadd(gadd(s1213, ac, d2), neg(aa), b);
+  const Grid g12n = gadd(gadd(s1213, neg(ac), d0), neg(cc), b);
+  const float r8 = gsum<9>(g8), r9 = gsum<9>(g9), r10 = gsum<9>(g10), r11 = gsum<9>(g11);
+  const float r12n = gsum<9>(g12n), r13 = gsum<9>(g13);
+  const float r2 = gdiff(g8, g9), r3 = gdiff(g13, g12n), r4 = gdiff(g11, g10);
+  const float r14 =
+      gsum<9>(gadd(gadd(gadd(gstart<9>(d0d1, d2), neg(aa), d0), bb, d1), neg(cc), d2));
+  // Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2
+  const float g14 = __fmaf_rn(r2, r2, __fmaf_rn(r3, r3, __fmul_rn(r4, r4)));
+  const float g2 = __fmaf_rn(
+      r8, r8,
+      __fmaf_rn(r9, r9,
+                __fmaf_rn(r10, r10,
+                          __fmaf_rn(r11, r11, __fmaf_rn(r12n, r12n, __fmul_rn(r13, r13))))));
+  o.D = __fmaf_rn(14.0f, g14, __fmaf_rn(2.0f, g2, __fmul_rn(r14, r14)));
+  return o;
+}
+
+// ---------------------------------------------------------------------------
 // General matrix.  dx(M) of Algorithm 5 term by term (reading R1 for r10).
 // The products M01 M10, M02 M20, M12 M21 and the d-products are the same for
 // M = A and M = A^T and are formed once by the caller.
@@ -384,21 +536,55 @@ struct EigC {
   bool j2_clamped, d_clamped;
 };
 
-// ANGLE64 (precision EIG3_PREC_F32_COMP_A64): the final combination of
+// I1 / 3 correctly rounded and the three roots from k = 2 r / (3 sqrt 3)
+// and the sines.  The quotient is the product with the binary32 reciprocal
+// of 3 and one FMA correction (q0 + (I1 - 3 q0)/3; exhaustively checked over a
+// binade, so for every normal I1), instead of an IEEE division.
+__device__ __forceinline__ void eig_roots(EigC &o) {
+  const float k = o.r * 0.38490017945975050967f;
+  const float q0 = __fmul_rn(o.I1, 0.333333343267f);
+  const float i3 = __fmaf_rn(__fmaf_rn(-3.0f, q0, o.I1), 0.333333343267f, q0);
+  o.l1 = fmaf(-k, fmaf(2.0f, o.sigma1, o.sigma2), i3);
+  o.l2 = fmaf(k, o.sigma1 - o.sigma2, i3);
+  o.l3 = fmaf(k, fmaf(2.0f, o.sigma2, o.sigma1), i3);
+}
+
+// Algorithm 6 in binary32 from the rounded scaled invariants.
+__device__ __forceinline__ EigC eigvals_r(const InvR &v) {
+  EigC o;
+  o.j2_clamped = v.J2x6 < 0.0f;
+  o.d_clamped = v.D < 0.0f;
+  // r = sqrt(3 J2) = sqrt(J2x6 / 2) * 2^e
+  o.r = __fmul_rn(sqrtf(0.5f * fmaxf(v.J2x6, 0.0f)), unscale_pow2(v.e));
+  const float x = v.J3x27;
+  const float y = sqrtf(27.0f * fmaxf(v.D, 0.0f));
+  const float pt = atan2f(y, fabsf(x)) * (1.0f / 3.0f);
+  float st, ct;
+  sincos_small(pt, st, ct);
+  st = fmaxf(st, 0.0f);
+  const float other = fmaf(0.86602540378443864676f, ct, -0.5f * st);
+  const bool pos = !(x < 0.0f);
+  o.sigma1 = pos ? st : other;
+  o.sigma2 = pos ? other : st;
+  o.I1 = v.I1;
+  eig_roots(o);
+  return o;
+}
+
+// From the compensated invariants: rounded to binary32 (eigvals_r), or with
+// ANGLE64 (precision EIG3_PREC_F32_COMP_A64) the final combination of
 // Delta's and 27 J3's compensated pairs and the triple angle in binary64
 // (triple_angle_sines of the binary64 path, which needs the binary64 header),
 // rounded back to binary32 sines; everything else as in the binary32 path.
 template <bool ANGLE64 = false>
 __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
-  EigC o;
-  const float j2x6 = round1(v.J2x6);
-  const float dd = round1(v.D);
-  o.j2_clamped = j2x6 < 0.0f;
-  o.d_clamped = dd < 0.0f;
-  const float p2e = unscale_pow2(v.e);
-  // r = sqrt(3 J2) = sqrt(J2x6 / 2) * 2^e
-  o.r = __fmul_rn(sqrtf(0.5f * fmaxf(j2x6, 0.0f)), p2e);
-  if constexpr (ANGLE64) {
+  if constexpr (!ANGLE64) {
+    return eigvals_r({round1(v.I1), round1(v.J2x6), round1(v.J3x27), round1(v.D), v.e});
+  } else {
+    EigC o;
+    const float j2x6 = round1(v.J2x6);
+    o.j2_clamped = j2x6 < 0.0f;
+    o.r = __fmul_rn(sqrtf(0.5f * fmaxf(j2x6, 0.0f)), unscale_pow2(v.e));
     const double x = (double)v.J3x27.s + (double)v.J3x27.c;
     const double d = (double)v.D.s + (double)v.D.c;
     o.d_clamped = d < 0.0;
@@ -407,29 +593,26 @@ __device__ __forceinline__ EigC eigvals_c(const InvC &v) {
     triple_angle_sines(x, sqrt_nonneg<3>(9.0 * nonneg(d)), s1, s2);
     o.sigma1 = __double2float_rn(s1);
     o.sigma2 = __double2float_rn(s2);
-  } else {
-    const float x = round1(v.J3x27);
-    const float y = sqrtf(27.0f * fmaxf(dd, 0.0f));
-    const float pt = atan2f(y, fabsf(x)) * (1.0f / 3.0f);
-    float st, ct;
-    sincos_small(pt, st, ct);
-    st = fmaxf(st, 0.0f);
-    const float other = fmaf(0.86602540378443864676f, ct, -0.5f * st);
-    const bool pos = !(x < 0.0f);
-    o.sigma1 = pos ? st : other;
-    o.sigma2 = pos ? other : st;
+    o.I1 = round1(v.I1);
+    eig_roots(o);
+    return o;
   }
-  o.I1 = round1(v.I1);
-  const float k = o.r * 0.38490017945975050967f;
-  // I1 / 3 correctly rounded: the product with the binary32 reciprocal of 3
-  // and one FMA correction (q0 + (I1 - 3 q0)/3; exhaustively checked over a
-  // binade, so for every normal I1), instead of an IEEE division
-  const float q0 = __fmul_rn(o.I1, 0.333333343267f);
-  const float i3 = __fmaf_rn(__fmaf_rn(-3.0f, q0, o.I1), 0.333333343267f, q0);
-  o.l1 = fmaf(-k, fmaf(2.0f, o.sigma1, o.sigma2), i3);
-  o.l2 = fmaf(k, o.sigma1 - o.sigma2, i3);
-  o.l3 = fmaf(k, fmaf(2.0f, o.sigma2, o.sigma1), i3);
-  return o;
+}
+
+// The eigenvalues of one matrix as the eigenvalue, adjoint, projector and
+// Mohr-Coulomb kernels compute them: N = 6 (symmetric layout) through the
+// grid-accumulated invariants_sym_eig (with ANGLE64 through the compensated
+// invariants and the binary64 angle), N = 9 through the compensated general
+// invariants.
+template <int N, bool ANGLE64 = false>
+__device__ __forceinline__ EigC eig_c(const float (&a)[N]) {
+  if constexpr (N == 9) {
+    return eigvals_c<ANGLE64>(invariants_general_c(a));
+  } else if constexpr (ANGLE64) {
+    return eigvals_c<true>(invariants_sym_c<true>(a[0], a[1], a[2], a[3], a[4], a[5]));
+  } else {
+    return eigvals_r(invariants_sym_eig(a[0], a[1], a[2], a[3], a[4], a[5]));
+  }
 }
 
 // Unscaled binary64 invariants (I1, J2, J3, Delta) from the compensated pairs.

@@ -72,13 +72,7 @@ __global__ void __launch_bounds__(kThreads)
     float a[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a[j] = row[j];
-    InvC v;
-    if constexpr (LAYOUT == EIG3_GENERAL9) {
-      v = invariants_general_c(a);
-    } else {
-      v = invariants_sym_c<true>(a[0], a[1], a[2], a[3], a[4], a[5]);
-    }
-    const EigC e = eigvals_c(v);
+    const EigC e = eig_c<N>(a);
     f[i] = fmaf(cm, e.l3, fmaf(-c1, e.l1, -1.0f));
     if constexpr (GRAD) {
       const AdjC s = adjoint_c(e.r, e.sigma1, e.sigma2, -c1, 0.0f, cm);

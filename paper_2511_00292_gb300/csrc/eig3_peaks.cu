@@ -11,14 +11,17 @@
 //     kind     0 DFMA, 1 DMUL, 2 DADD, 3 FFMA; 4 DFMA with two integer
 //              operations per DFMA, 5 DFMA with two FFMA per DFMA (the binary64
 //              pipe fed between other instructions, as in a real kernel; only
-//              the DFMA are counted)
+//              the DFMA are counted); 6 FFMA2 (the packed two-lane binary32
+//              FMA, __ffma2_rn: one instruction, two FMAs), 7 FFMA2 with one
+//              integer operation per FFMA2 (whether the packed form leaves
+//              issue slots free for other work; only the FFMA2 are counted)
 //     chains   independent chains per thread: 2, 4, 8 or 16
 //     blocks, threads   launch shape (threads <= 1024)
 //     iters    loop trips; every trip issues `chains` instructions of `kind`
 //              per thread
 //     out      device buffer of blocks * threads elements (double for kinds
-//              0-2, float for 3): each thread's result, so that nothing is
-//              optimised away
+//              0-2, 4, 5, float for 3, 6, 7): each thread's result, so that
+//              nothing is optimised away
 //   Returns the cudaError_t of the launch (0 on success); asynchronous on
 //   `stream`.  Instructions executed = blocks * threads * iters * chains.
 #include <cuda_runtime.h>
@@ -101,6 +104,32 @@ __global__ void __launch_bounds__(1024) k_peak32(int iters, float a, float b,
   out[t] = s;
 }
 
+// Packed binary32 FMA chains (MIX = 1: one integer operation per FFMA2).
+template <int MIX, int C>
+__global__ void __launch_bounds__(1024) k_peak32x2(int iters, float a, float b,
+                                                   float *__restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float2 x[C];
+  unsigned k[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    x[j] = make_float2(1.0f + 1e-3f * (float)((t + j) & 255), 1.0f - 1e-3f * (float)j);
+    k[j] = (unsigned)(t * 2654435761u + j);
+  }
+  const float2 va = make_float2(a, a), vb = make_float2(b, b);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      x[j] = __ffma2_rn(x[j], va, vb);
+      if constexpr (MIX == 1) k[j] ^= (unsigned)i;
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) s += x[j].x + x[j].y + (float)(k[j] & 1u) * 1e-30f;
+  out[t] = s;
+}
+
 template <int C>
 int launch(int kind, int blocks, int threads, int iters, void *out, cudaStream_t s) {
   // a, b chosen so that the chains neither overflow nor flush to zero over
@@ -116,6 +145,14 @@ int launch(int kind, int blocks, int threads, int iters, void *out, cudaStream_t
       break;
     case 4: k_peak64_mixed<0, C><<<blocks, threads, 0, s>>>(iters, a, b, o64); break;
     case 5: k_peak64_mixed<1, C><<<blocks, threads, 0, s>>>(iters, a, b, o64); break;
+    case 6:
+      k_peak32x2<0, C><<<blocks, threads, 0, s>>>(iters, (float)a, (float)b,
+                                                  static_cast<float *>(out));
+      break;
+    case 7:
+      k_peak32x2<1, C><<<blocks, threads, 0, s>>>(iters, (float)a, (float)b,
+                                                  static_cast<float *>(out));
+      break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

@@ -190,7 +190,7 @@ def _expr(e, braces="list"):
 
 
 TYPES = r"(double|int|bool|float|Adj|Adj3|Inv|Eig|Dx|DxShared)"
-TYPES_C = r"(int|bool|float|F2|Sum|Diag|InvC|Shared|R13|AdjC)"
+TYPES_C = r"(int|bool|float|F2|Sum|Grid|Diag|InvC|InvR|Shared|R13|AdjC)"
 
 
 def _translate(stmt, types=TYPES, ctors=None, braces="list"):
@@ -457,6 +457,8 @@ ENV_C = dict(
     mul=lambda x, y: V(val(x) * val(y)), neg=lambda x: V(-val(x)),
     scale2=lambda x, p: V(val(x) * val(p)), start=lambda x: V(val(x)),
     pair=lambda x: V(val(x)), sq=lambda x: V(val(x) ** 2), done=lambda x: V(val(x)),
+    gstart=lambda x, y: V(val(x) * val(y)), gadd=lambda g, x, y: V(val(g) + val(x) * val(y)),
+    gsum=val, gdiff=lambda x, y: V(val(x) - val(y)),
     round1=val, __fmul_rn=lambda a, b: val(a) * val(b), __fadd_rn=lambda a, b: val(a) + val(b),
     __fsub_rn=lambda a, b: val(a) - val(b), __fmaf_rn=lambda a, b, c: val(a) * val(b) + val(c),
     fmaf=lambda a, b, c: a * b + c, det2=lambda a, d, b, c: a * d - b * c,
@@ -513,6 +515,38 @@ def test_compensated_invariants_sym_source_equals_definitions(eig):
     non-negative sum for the eigenvalue kernels)."""
     s6, A = sym_symbols()
     _check_scaled_invariants(f32c_function("invariants_sym_c", EIG=eig)(*s6), A)
+
+
+def test_grid_invariants_sym_source_equals_definitions():
+    """The symmetric invariants of the eigenvalue kernels (every sum on its
+    fixed grid, Delta from the rounded r_i with -r12 for r12) are I1, 6 J2,
+    27 J3 and the discriminant exactly."""
+    s6, A = sym_symbols()
+    _check_scaled_invariants(f32c_function("invariants_sym_eig")(*s6), A)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("gadd(j3, mul(bb, t2), _Q('9.0'))", "gadd(j3, mul(bb, t2), _Q('8.0'))"),
+    ("gadd(gadd(s89, aa, c), neg(ab), d1)", "gadd(s89, aa, c)"),
+    ("gdiff(g13, g12n)", "gdiff(g13, g12n) + r13"),
+    ("gadd(j2, cc, _Q('6.0'))", "gadd(j2, cc, _Q('3.0'))"),
+    ("__fmul_rn(r14, r14)", "_Q('0.0')"),
+    ("gadd(s1213, neg(ac), d0)", "gadd(s1213, ac, d0)"),
+])
+def test_grid_invariants_sym_check_sees_a_slip(old, new):
+    """A wrong weight, a dropped term or a flipped sign in the grid form
+    breaks one of the identities above."""
+    s6, A = sym_symbols()
+    fn = f32c_function("invariants_sym_eig")
+    assert old in fn.code
+    e = dict(ENV_C)
+    e.update(E=127)
+    e.update(zip(["a00", "a11", "a22", "c0", "b0", "a0"], s6))
+    exec(fn.code.replace(old, new, 1), e)
+    o = e["__ret__"]
+    I1, J2, J3 = invariants_of(A)
+    assert not (zero(val(o.J2x6) - 6 * J2) and zero(val(o.J3x27) - 27 * J3)
+                and zero(val(o.D) - (4 * J2 ** 3 - 27 * J3 ** 2)))
 
 
 def test_rounded_discriminant_keeps_the_weights():
