@@ -197,6 +197,39 @@ __device__ __forceinline__ double times_pow2_sat(double x, int k) {
   return r;
 }
 
+// x 2^k exactly as the binary64 product x * 2^k rounds it, for any x and
+// |k| < 2^11, by integer operations on the bits (no FP64-pipe instruction):
+// a subnormal x is normalised first, a result below the normal range is
+// rounded to nearest even into the subnormals, one beyond it is +-infinity,
+// zero and non-finite x are returned unchanged.  For the rescalings of the
+// rare out-of-range data (whose FP64 multiplications were issued, predicated
+// off, by every warp) and for the powers of two of the fused adjoint.
+__device__ __forceinline__ double scale2k(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long sign = b & 0x8000000000000000ull;
+  const unsigned long long mag = b ^ sign;
+  int E = (int)(mag >> 52);
+  if (E == 0x7ff || mag == 0) return x;
+  unsigned long long m;
+  if (E == 0) {
+    const int s = __clzll((long long)mag) - 11;
+    m = mag << s;
+    E = 1 - s;
+  } else {
+    m = (mag & 0xfffffffffffffull) | 0x10000000000000ull;
+  }
+  const int ne = E + k;
+  if (ne >= 0x7ff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
+  if (ne >= 1)
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)ne << 52) | (m & 0xfffffffffffffull)));
+  const int sh = 1 - ne;  // >= 1: the result is subnormal (or rounds up to 2^-1022)
+  if (sh > 54) return __longlong_as_double((long long)sign);
+  const unsigned long long q = m >> sh, rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  const unsigned long long r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  return __longlong_as_double((long long)(sign | r));
+}
+
 // |x| by clearing the sign bit (integer pipe, in PTX for the same reason: a
 // floating-point absolute value would take an FP64-pipe slot).
 __device__ __forceinline__ double abs_bits64(double x) {
@@ -228,9 +261,8 @@ __device__ __forceinline__ int dev_scale(double (&v)[N]) {
   int e = 0;
   if (E < 1023 - 150 || E >= 1023 + 150) {
     e = min(max(E, 1), 2045) - 1023;  // zero / subnormal data: scale by 2^1022
-    const double sc = pow2d(-e);
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] *= sc;
+    for (int j = 0; j < N; ++j) v[j] = scale2k(v[j], -e);
   }
   return e;
 }
@@ -809,10 +841,10 @@ __device__ __forceinline__ EigV eigvals_vjp_fwd(const Inv &v) {
   o.kKm = kK * o.m;
   // k = kK r of A itself = kK m 2^(kr + e): for unscaled data (e = 0) the
   // exponent is added on the integer pipe (kK m 2^kr is a normal number:
-  // J2+ >= 2^-1074 keeps r above 2^-537), otherwise by exact multiplications
-  // that over- or underflow like the product itself
+  // J2+ >= 2^-1074 keeps r above 2^-537), otherwise by two exact scalings
+  // (scale2k) that round, over- and underflow like the products themselves
   const double k =
-      (v.e == 0) ? times_pow2(o.kKm, o.kr) : o.kKm * pow2d(o.kr) * pow2d(v.e);
+      (v.e == 0) ? times_pow2(o.kKm, o.kr) : scale2k(scale2k(o.kKm, o.kr), v.e);
   o.e.r = o.m;  // r of the scaled data up to 2^kr (the fused kernel stores no r)
   const double i3 = v.I1 * kInv3;
   o.c12 = fma(2.0, o.e.sigma1, o.e.sigma2);
@@ -862,14 +894,15 @@ __device__ __forceinline__ Adj adjoint_vjp(const EigV &f, double g1, double g2, 
 // scaled deviatoric data stay inside 2^+-448 (always, but for J2 tiny against
 // the data of a nearly defective matrix), b2 = a_J2 2^k 2^-k and b3 = a_J3
 // 2^2k 2^-2k; otherwise b2, b3 stay as carried and the data and products are
-// shifted by 2^-k and 2^-2k instead.  The shift returned (0 in range) is
-// applied by exponent arithmetic (times_pow2), so both cases run the same
-// FP64 instructions and no lane idles on the other case's.
+// shifted by 2^-k and 2^-2k instead.  The scalings of b2, b3 (exact, as the
+// products by 2^-k and 2^-2k would round) and the shift returned (0 in
+// range, applied by times_pow2_sat) are integer operations, so neither case
+// takes an FP64-pipe slot.
 __device__ __forceinline__ int vjp_units(const Adj &s, int hmax, double &b2, double &b3) {
   const int E = hmax >> 20;
   const bool in_range = E >= 1023 - 448 && E <= 1023 + 448 && s.k >= -448 && s.k <= 448;
-  const double u2 = s.aJ2s * pow2d(in_range ? -s.k : 0);
-  const double u3 = s.aJ3s * pow2d(in_range ? -2 * s.k : 0);
+  const double u2 = scale2k(s.aJ2s, in_range ? -s.k : 0);
+  const double u3 = scale2k(s.aJ3s, in_range ? -2 * s.k : 0);
   b2 = u2;
   b3 = u3;
   return in_range ? 0 : -s.k;
