@@ -926,26 +926,23 @@ __device__ __forceinline__ void grad_general_vjp(const ShareG &x, double J2, con
 #pragma unroll
     for (int j = 0; j < 10; ++j) P[j] = times_pow2_sat(P[j], 2 * sh);
   }
-  double C[9];
-  C[0] = fma(D[4], D[8], -P[0]);
-  C[1] = fma(-D[3], D[8], P[1]);
-  C[2] = fma(-D[4], D[6], P[2]);
-  C[3] = fma(-D[1], D[8], P[3]);
-  C[4] = fma(D[0], D[8], -P[4]);
-  C[5] = fma(-D[0], D[7], P[5]);
-  C[6] = fma(-D[2], D[4], P[6]);
-  C[7] = fma(-D[0], D[5], P[7]);
-  C[8] = fma(D[0], D[4], -P[8]);
+  // diagonal: b2 S_ii + b3 C_ii + base, C_ii the 2x2 minors
+  const double C0 = fma(D[4], D[8], -P[0]);
+  const double C4 = fma(D[0], D[8], -P[4]);
+  const double C8 = fma(D[0], D[4], -P[8]);
   const double base = fma(b3, P[9] * kInv3, s.aI1);  // -a_J3 tr(cof S) / 3
-  G[0] = fma(b2, D[0], fma(b3, C[0], base));
-  G[1] = fma(b2, D[3], b3 * C[1]);
-  G[2] = fma(b2, D[6], b3 * C[2]);
-  G[3] = fma(b2, D[1], b3 * C[3]);
-  G[4] = fma(b2, D[4], fma(b3, C[4], base));
-  G[5] = fma(b2, D[7], b3 * C[5]);
-  G[6] = fma(b2, D[2], b3 * C[6]);
-  G[7] = fma(b2, D[5], b3 * C[7]);
-  G[8] = fma(b2, D[8], fma(b3, C[8], base));
+  G[0] = fma(b2, D[0], fma(b3, C0, base));
+  G[4] = fma(b2, D[4], fma(b3, C4, base));
+  G[8] = fma(b2, D[8], fma(b3, C8, base));
+  // off-diagonal: b2 S_ji + b3 (P - S_ji S_kk) = S_ji (b2 - b3 S_kk) + b3 P, the
+  // bracket shared by the two entries with the same S_kk
+  const double q0 = fma(-b3, D[0], b2), q4 = fma(-b3, D[4], b2), q8 = fma(-b3, D[8], b2);
+  G[1] = fma(D[3], q8, b3 * P[1]);
+  G[3] = fma(D[1], q8, b3 * P[3]);
+  G[2] = fma(D[6], q4, b3 * P[2]);
+  G[6] = fma(D[2], q4, b3 * P[6]);
+  G[5] = fma(D[7], q0, b3 * P[5]);
+  G[7] = fma(D[5], q0, b3 * P[7]);
 }
 
 // The symmetric form (gradient with respect to the six stored entries, as

@@ -417,6 +417,86 @@ def test_grad_sym_source_is_the_chain_rule():
         assert zero(G[idx] - want), idx
 
 
+def _struct_fields(name):
+    body = re.search(r"struct " + name + r" \{(.*?)\};", _source(), re.S).group(1)
+    body = re.sub(r"//[^\n]*", "", body)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            out += [f.strip() for f in re.sub(r"^\w+\s+", "", decl).split(",")]
+    return out
+
+
+def _shared_of(inv_name, struct, args):
+    """Run the invariants function's source and build the products it hands
+    on to the fused kernel from its own `*x = Struct{...}` initializer."""
+    fn = device_function(inv_name)
+    env = dict(BASE_ENV)
+    params, body = _definition(_source(), inv_name)
+    env.update(zip(params, args))
+    exec(fn.code, env)
+    init = re.search(r"\*x = " + struct + r"\{(.*?)\};", body, re.S).group(1)
+    vals = [eval(_expr(e.strip()), env) for e in _split_top(init, ",")]
+    fields = _struct_fields(struct)
+    assert len(vals) == len(fields)
+    return NS(**dict(zip(fields, vals))), env["__ret__"]
+
+
+def _fused_grad(name, x, J2, aI1, b2, b3, n):
+    fn = device_function(name)
+    code = fn.code.replace("b2 = NS()", "b2 = s.aJ2s").replace("b3 = NS()", "b3 = s.aJ3s")
+    G = [None] * n
+    env = dict(BASE_ENV)
+    env.update(x=x, J2=J2, s=NS(aI1=aI1, aJ2s=b2, aJ3s=b3, k=0, rz=False), G=G)
+    exec(code, env)
+    return G
+
+
+def test_fused_grad_general_source_is_the_chain_rule():
+    """The fused kernel's gradient (grad_general_vjp, at k = 0: the scalings
+    are the identity) on the products invariants_general hands on is
+    a_I1 dI1/dA + a_J2 dJ2/dA + a_J3 dJ3/dA, entry by entry."""
+    a, A = general_symbols()
+    aI1, b2, b3 = sp.symbols("aI1 aJ2 aJ3", real=True)
+    x, inv = _shared_of("invariants_general", "ShareG", [a])
+    G = _fused_grad("grad_general_vjp", x, inv.J2, aI1, b2, b3, 9)
+    I1, J2, J3 = invariants_of(A)
+    assert zero(inv.J2 - J2)
+    for idx in range(9):
+        want = aI1 * sp.diff(I1, a[idx]) + b2 * sp.diff(J2, a[idx]) + b3 * sp.diff(J3, a[idx])
+        assert zero(G[idx] - want), idx
+
+
+def test_fused_grad_sym_source_is_the_chain_rule():
+    s6, A = sym_symbols()
+    aI1, b2, b3 = sp.symbols("aI1 aJ2 aJ3", real=True)
+    x, inv = _shared_of("invariants_sym", "ShareS", [s6])
+    G = _fused_grad("grad_sym_vjp", x, inv.J2, aI1, b2, b3, 6)
+    I1, J2, J3 = invariants_of(A)
+    for idx in range(6):
+        want = aI1 * sp.diff(I1, s6[idx]) + b2 * sp.diff(J2, s6[idx]) + b3 * sp.diff(J3, s6[idx])
+        assert zero(G[idx] - want), idx
+
+
+def test_fused_grad_check_sees_a_slip():
+    """A transposed operand in the shared bracket breaks the identity above."""
+    a, A = general_symbols()
+    aI1, b2, b3 = sp.symbols("aI1 aJ2 aJ3", real=True)
+    x, inv = _shared_of("invariants_general", "ShareG", [a])
+    fn = device_function("grad_general_vjp")
+    code = fn.code.replace("b2 = NS()", "b2 = s.aJ2s").replace("b3 = NS()", "b3 = s.aJ3s")
+    old = "G[1] = fma(D[3], q8, b3 * P[1])"
+    assert old in code
+    G = [None] * 9
+    env = dict(BASE_ENV)
+    env.update(x=x, J2=inv.J2, s=NS(aI1=aI1, aJ2s=b2, aJ3s=b3, k=0, rz=False), G=G)
+    exec(code.replace(old, "G[1] = fma(D[1], q8, b3 * P[1])"), env)
+    I1, J2, J3 = invariants_of(A)
+    want = aI1 * sp.diff(I1, a[1]) + b2 * sp.diff(J2, a[1]) + b3 * sp.diff(J3, a[1])
+    assert not zero(G[1] - want)
+
+
 # ---------------------------------------------------------------------------
 # The compensated binary32 source (csrc/eig3_f32c.cuh) in exact arithmetic
 # ---------------------------------------------------------------------------
