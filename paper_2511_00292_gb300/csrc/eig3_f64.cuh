@@ -157,6 +157,22 @@ __device__ __forceinline__ double recip_pos(double x) {
   return __hiloint2double(__double2hiint(c) - (k << 20), __double2loint(c));
 }
 
+// 1/(3x) for a positive normal x, as recip_pos: the binary32 seed of
+// 1/(3x') is cut to 22 significant bits so that its triple is exact in
+// binary32, and e = 1 - x' (3 c0) is one FMA; three FP64-pipe instructions,
+// the factor 1/3 costing none.
+__device__ __forceinline__ double recip3_pos(double x) {
+  const int hi = __double2hiint(x);
+  const int k = ((hi >> 20) & 0x7ff) - 1023;
+  const double xs = __hiloint2double(hi - (k << 20), __double2loint(x));
+  const float cf =
+      __int_as_float(__float_as_int(rcp_seed(seed_float(xs)) * (1.0f / 3.0f)) & ~3);
+  const double c0 = widen(cf);
+  const double e = fma(-xs, widen(3.0f * cf), 1.0);
+  const double c = fma(c0, fma(e, e, e), c0);
+  return __hiloint2double(__double2hiint(c) - (k << 20), __double2loint(c));
+}
+
 // x 2^k by adding k to the exponent field (integer pipe): exact for normal x
 // whose result stays below the overflow threshold, which the caller ensures
 // (|k| small, |x| far from it).  Zero, subnormal and non-finite x are
@@ -521,10 +537,10 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   const double eta0 = (cc - 1.0) + ss;
   const double f0 = fma(eta0, fma(eta0, 0.375, -0.5), 1.0);
   const double ef = f0 * eps;
-  const double cef = fma(-0.5 * eps, ef, f0);
+  const double cef = fma(-times_pow2(eps, -1), ef, f0);  // eps/2 on the integer pipe
   const double ct = fma(c0, cef, -(s0 * ef));
   const double st = nonneg(fma(s0, cef, c0 * ef));
-  const double other = fma(kHalfSqrt3, ct, -0.5 * st);  // sin(pi/3 - psi~)
+  const double other = fma(kHalfSqrt3, ct, -times_pow2(st, -1));  // sin(pi/3 - psi~)
   // sign test on the bits: x = -0 goes with x < 0, as atan2(0, -0) = pi does
   const bool pos = __double2hiint(x) >= 0;
   sigma1 = pos ? st : other;
@@ -589,6 +605,7 @@ __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
 // --------------------------------------------------------------------------
 struct Adj {
   double aI1, aJ2s, aJ3s;  // a_I1, a_J2 2^k, a_J3 2^2k
+  double n2, g2;           // adjoint_vjp: a_I1 = g2 + n2 / 3, finished in the gradient
   int k;                   // r = m 2^k; 0 when r = 0
   bool rz;                 // r = 0 (or subnormal): a triple eigenvalue, a_J2 = a_J3 = 0
 };
@@ -858,7 +875,8 @@ __device__ __forceinline__ EigV eigvals_vjp_fwd(const Inv &v) {
 // the scaled frame) from the forward's m, kr, kK m and 2 sigma1 + sigma2:
 //   D23 = n23 s1 (s3 Rh),  D23 - D12 = D23 - n12 s2 (s3 Rh),
 //   a_J3 2^2k = (D23 - D12) s1 s2 Rh,  a_J2 2^k = D23 - kK m (2 s1 + s2) a_J3 2^2k,
-// with Rh = (sqrt3/2) / (m s1 s2 s3), and a_I1 = g2 + (n23 - n12)/3.
+// with Rh = (sqrt3/2) / (m s1 s2 s3), and a_I1 = g2 + (n23 - n12)/3 (the
+// last step in the gradient).
 __device__ __forceinline__ Adj adjoint_vjp(const EigV &f, double g1, double g2, double g3) {
   const double sigma1 = f.e.sigma1, sigma2 = f.e.sigma2;
   const bool z1 = hi_abs(sigma1) < (63 << 20);
@@ -866,14 +884,17 @@ __device__ __forceinline__ Adj adjoint_vjp(const EigV &f, double g1, double g2, 
   const double s1 = z1 ? 1.0 : sigma1, s2 = z2 ? 1.0 : sigma2;
   const double s3 = sigma1 + sigma2;
   const bool rz = hi_abs(f.m) < (1 << 20);  // r = 0: a triple eigenvalue
-  const double m = rz ? 1.0 : f.m;
+  const double km = rz ? kK : f.kKm;         // kK m, m = 1 for r = 0
   const double s12 = s1 * s2;
   const double P = s12 * s3;
-  const double R = recip_pos(m * P);
-  const double Rh = kHalfSqrt3 * R;
+  // Rh = (sqrt3/2) / (m P) = 1 / (3 kK m P): the factor in the seed (recip3_pos)
+  const double Rh = recip3_pos(km * P);
   double n12 = g2 - g1, n23 = g3 - g2;
   Adj o;
-  o.aI1 = fma(n23 - n12, kInv3, g2);
+  // a_I1 = (g1 + g2 + g3)/3 = g2 + (n23 - n12)/3, finished in the gradient's
+  // diagonal constant (grad_*_vjp)
+  o.n2 = n23 - n12;
+  o.g2 = g2;
   if (z1 || z2) {  // an exactly coalesced pair takes the mean of its two weights
     n12 = z1 ? 0.0 : 0.5 * (g2 + g3) - g1;
     n23 = z2 ? 0.0 : g3 - 0.5 * (g1 + g2);
@@ -930,7 +951,8 @@ __device__ __forceinline__ void grad_general_vjp(const ShareG &x, double J2, con
   const double C0 = fma(D[4], D[8], -P[0]);
   const double C4 = fma(D[0], D[8], -P[4]);
   const double C8 = fma(D[0], D[4], -P[8]);
-  const double base = fma(b3, P[9] * kInv3, s.aI1);  // -a_J3 tr(cof S) / 3
+  // a_I1 - a_J3 tr(cof S) / 3 = g2 + (n23 - n12 + a_J3 J2) / 3
+  const double base = fma(fma(b3, P[9], s.n2), kInv3, s.g2);
   G[0] = fma(b2, D[0], fma(b3, C0, base));
   G[4] = fma(b2, D[4], fma(b3, C4, base));
   G[8] = fma(b2, D[8], fma(b3, C8, base));
@@ -970,7 +992,7 @@ __device__ __forceinline__ void grad_sym_vjp(const ShareS &x, double J2, const A
   const double C12 = fma(-S00, D[3], P[3]);
   const double C02 = fma(-S11, D[4], P[4]);
   const double C01 = fma(-S22, D[5], P[5]);
-  const double base = fma(b3, P[6] * kInv3, s.aI1);
+  const double base = fma(fma(b3, P[6], s.n2), kInv3, s.g2);
   const double b2x2 = 2.0 * b2, b3x2 = 2.0 * b3;
   G[0] = fma(b2, D[0], fma(b3, C00, base));
   G[1] = fma(b2, D[1], fma(b3, C11, base));

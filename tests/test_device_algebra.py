@@ -417,6 +417,23 @@ def test_grad_sym_source_is_the_chain_rule():
         assert zero(G[idx] - want), idx
 
 
+def test_fused_adjoint_scalars_are_root_derivatives():
+    """adjoint_vjp (k = 0, no coalescence): a_J2 and a_J3 are the weighted
+    derivatives of the roots of the depressed cubic, from the forward's m,
+    kK m and 2 sigma1 + sigma2, with Rh = 1 / (3 kK m P) from recip3_pos; and
+    a_I1 = g2 + n2 / 3 is the mean weight."""
+    r, s1, s2 = sp.symbols("r sigma1 sigma2", positive=True)
+    g = sp.symbols("g1:4", real=True)
+    env = dict(BASE_ENV, recip3_pos=lambda x: 1 / (3 * x), hi_abs=lambda x: 0)
+    fn = device_function("adjoint_vjp", env=env, z1=False, z2=False, rz=False)
+    f = NS(e=NS(sigma1=s1, sigma2=s2), m=r, kKm=EXACT["kK"] * r, c12=2 * s1 + s2, kr=0)
+    o = fn(f, *g)
+    _, aJ2, aJ3 = _roots_derivatives(r, s1, s2, g)
+    assert sp.simplify(o.aJ3s - aJ3) == 0
+    assert sp.simplify(o.aJ2s - aJ2) == 0
+    assert sp.simplify(o.g2 + o.n2 / 3 - sum(g) / 3) == 0
+
+
 def _struct_fields(name):
     body = re.search(r"struct " + name + r" \{(.*?)\};", _source(), re.S).group(1)
     body = re.sub(r"//[^\n]*", "", body)
@@ -448,9 +465,11 @@ def _fused_grad(name, x, J2, aI1, b2, b3, n):
     code = fn.code.replace("b2 = NS()", "b2 = s.aJ2s").replace("b3 = NS()", "b3 = s.aJ3s")
     G = [None] * n
     env = dict(BASE_ENV)
-    env.update(x=x, J2=J2, s=NS(aI1=aI1, aJ2s=b2, aJ3s=b3, k=0, rz=False), G=G)
+    g2 = sp.Symbol("g2_weight", real=True)
+    env.update(x=x, J2=J2, s=NS(n2=3 * aI1 - 3 * g2, g2=g2, aJ2s=b2, aJ3s=b3, k=0, rz=False),
+               G=G)
     exec(code, env)
-    return G
+    return [sp.expand(gi) for gi in G]
 
 
 def test_fused_grad_general_source_is_the_chain_rule():
@@ -490,7 +509,7 @@ def test_fused_grad_check_sees_a_slip():
     assert old in code
     G = [None] * 9
     env = dict(BASE_ENV)
-    env.update(x=x, J2=inv.J2, s=NS(aI1=aI1, aJ2s=b2, aJ3s=b3, k=0, rz=False), G=G)
+    env.update(x=x, J2=inv.J2, s=NS(n2=3 * aI1, g2=0, aJ2s=b2, aJ3s=b3, k=0, rz=False), G=G)
     exec(code.replace(old, "G[1] = fma(D[1], q8, b3 * P[1])"), env)
     I1, J2, J3 = invariants_of(A)
     want = aI1 * sp.diff(I1, a[1]) + b2 * sp.diff(J2, a[1]) + b3 * sp.diff(J3, a[1])

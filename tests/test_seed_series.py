@@ -78,6 +78,24 @@ def test_reciprocal_series_is_faithful():
     assert worst < 0.51
 
 
+def test_reciprocal_of_three_x_series_is_faithful():
+    """recip3_pos: 1/(3 x') from a seed of 1/(3 x') cut to 22 bits (its
+    triple exact in binary32), e = 1 - x' (3 c0), the same series."""
+    rng = random.Random(31)
+    worst = 0.0
+    for xs in [1.0, 2.0 - 2 ** -51, 1.5, 4.0 / 3.0] + [rng.uniform(1.0, 2.0) for _ in range(4000)]:
+        c_exact = 1.0 / f32(trunc24(xs))
+        for rel in (-2 ** -22, 2 ** -22, rng.uniform(-2 ** -22, 2 ** -22)):
+            cf = trunc22(f32(f32(c_exact * (1.0 + rel)) * f32(1.0 / 3.0)))
+            c3 = f32(3.0 * cf)
+            assert c3 == 3.0 * cf                    # exact in binary32
+            e = fma(-xs, c3, 1.0)
+            cc = fma(cf, fma(e, e, e), cf)
+            worst = max(worst, ulp_error(cc, exact=1 / (3 * Fr(xs))))
+    print(f"1/(3x) worst {worst:.3f} ulp")
+    assert worst < 0.51
+
+
 def test_truncating_the_series_earlier_is_not_faithful():
     """The t^2 term of the square root matters: without it the error is far
     above one ulp for seeds at the allowed error (the check can fail)."""
