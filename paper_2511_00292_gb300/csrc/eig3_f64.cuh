@@ -567,7 +567,7 @@ __device__ __forceinline__ Eig eigvals_from_inv(const Inv &v) {
   const double J2p = nonneg(v.J2);
   const double Dp = nonneg(v.D);
   o.r = sqrt_nonneg<3>(J2p);
-  if (v.e != 0) o.r *= pow2d(v.e);
+  if (v.e != 0) o.r = scale2k(o.r, v.e);
   // (J3, sqrt(Delta/27)) has the direction of (27 J3, sqrt(27 Delta))
   triple_angle_sines(v.J3, sqrt_nonneg(Dp * kInv27), o.sigma1, o.sigma2);
   const double k = o.r * kK;
@@ -623,8 +623,7 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const int hr = hi_abs(r);
   const bool rz = hr < (1 << 20);  // r = 0 or subnormal: a triple eigenvalue
   const int kr = min((hr >> 20) - 1023, 1022);
-  const double p2k = pow2d(-kr);
-  const double m = rz ? 1.0 : r * p2k;
+  const double m = rz ? 1.0 : scale2k(r, -kr);  // r 2^-kr on the integer pipe
   const double s12 = s1 * s2;
   const double P = s12 * s3;
   const double R = recip_pos(m * P);
@@ -669,8 +668,7 @@ __device__ __forceinline__ Adj3 adjoint_units(double r, double sigma1, double si
   const int hr = hi_abs(r);
   const bool rz = hr < (1 << 20);
   const int kr = min((hr >> 20) - 1023, 1022);
-  const double p2k = pow2d(-kr);
-  const double m = rz ? 1.0 : r * p2k;
+  const double m = rz ? 1.0 : scale2k(r, -kr);  // r 2^-kr on the integer pipe
   const double s12 = s1 * s2;
   const double P = s12 * s3;
   const double R = recip_pos(m * P);
@@ -689,7 +687,7 @@ __device__ __forceinline__ Adj3 adjoint_units(double r, double sigma1, double si
     o.b3[k] = (D23 - D12) * X13;
     o.b2[k] = fma(c, o.b3[k], D23);
   }
-  o.inv_r = rz ? 0.0 : (P * R) * p2k;
+  o.inv_r = rz ? 0.0 : scale2k(P * R, -kr);
   return o;
 }
 
@@ -753,13 +751,18 @@ __device__ __forceinline__ void grad_units(double (&D)[N], const Adj &s, double 
 #pragma unroll
   for (int j = 1; j < N; ++j) h = max(h, hi_abs(D[j]));
   const int E = h >> 20;
+  // the powers of two by exponent arithmetic (scale2k, rounding as the
+  // products would): the rare branch's N multiplications were issued by every
+  // warp with its lanes predicated off
   if (E >= 1023 - 448 && E <= 1023 + 448 && s.k >= -448 && s.k <= 448) {
-    b2 *= pow2d(-s.k);
-    b3 *= pow2d(-2 * s.k);
+    b2 = scale2k(b2, -s.k);
+    b3 = scale2k(b3, -2 * s.k);
   } else {
-    const double sc = s.rz ? 0.0 : pow2d(-s.k);
+    // r = 0 (whose data are finite) takes D * 0: zeros of D's sign
 #pragma unroll
-    for (int j = 0; j < N; ++j) D[j] *= sc;
+    for (int j = 0; j < N; ++j)
+      D[j] = s.rz ? __hiloint2double(__double2hiint(D[j]) & (int)0x80000000, 0)
+                  : scale2k(D[j], -s.k);
   }
 }
 

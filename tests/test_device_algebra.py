@@ -240,7 +240,8 @@ def device_function(name, path=None, env=None, types=TYPES, ctors=None, braces="
 BASE_ENV = dict(
     _Q=sp.Rational, NS=NS, fma=lambda a, b, c: a * b + c,
     recip_pos=lambda x: 1 / x, pow2d=lambda k: sp.Integer(2) ** k,
-    times_pow2=lambda x, k: x * sp.Integer(2) ** k, **EXACT)
+    times_pow2=lambda x, k: x * sp.Integer(2) ** k, scale2k=lambda x, k: x * sp.Integer(2) ** k,
+    **EXACT)
 BASE_ENV["dx13"] = lambda *a: device_function("dx13")(*a)
 
 

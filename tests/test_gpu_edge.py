@@ -302,6 +302,17 @@ def test_zero_copy_pinned_host_buffers(eig3):
     l_h = eig3.eigvals(S.pin_memory(), precision="f32c", device=dev())
     torch.cuda.synchronize()
     assert torch.equal(l_h, eig3.eigvals(S.to(dev()), precision="f32c").cpu())
+    # the fused entry point on host pointers, both precisions
+    lv_h, gv_h = eig3.eigvals_vjp(hA, hw, device=dev())
+    torch.cuda.synchronize()
+    assert not gv_h.is_cuda and gv_h.is_pinned()
+    lv_d, gv_d = eig3.eigvals_vjp(dA, hw.to(dev()))
+    assert torch.equal(lv_h, lv_d.cpu()) and torch.equal(gv_h, gv_d.cpu())
+    wS = torch.randn(S.shape[0], 3, dtype=torch.float32).pin_memory()
+    ls_h, gs_h = eig3.eigvals_vjp(S.pin_memory(), wS, precision="f32c", device=dev())
+    torch.cuda.synchronize()
+    ls_d, gs_d = eig3.eigvals_vjp(S.to(dev()), wS.to(dev()), precision="f32c")
+    assert torch.equal(ls_h, ls_d.cpu()) and torch.equal(gs_h, gs_d.cpu())
     with pytest.raises(ValueError):
         eig3.eigvals(bt.A)          # pageable host memory is refused
 

@@ -59,3 +59,36 @@ def test_more_than_2_31_rows(eig3):
     err, tol, bad = U.check_eig_f64(U.to_np(lam64[idx]), X, np.ones(len(X)), SYM,
                                     f32_storage=True)
     assert not bad.any()
+
+
+def test_fused_beyond_2_31_rows(eig3):
+    """eig3_eigvals_vjp (the benchmark step's entry) on 2^31 + 77 rows of the
+    compensated binary32 half: eigenvalues equal eigvals' and every gradient
+    row equals the small-batch result for the same matrix and weights."""
+    dev = torch.device("cuda:0")
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 175e9:
+        pytest.skip("needs about 175 GB of free device memory")
+    base_n = 1 << 20
+    base = W.workload3(n=base_n, device=dev, seed=9303).A
+    wb = torch.randn(base_n, 3, dtype=torch.float32, device=dev,
+                     generator=torch.Generator(dev).manual_seed(9304))
+    tail = W.workload3(n=77, device=dev, seed=9305).A
+    wt = torch.randn(77, 3, dtype=torch.float32, device=dev,
+                     generator=torch.Generator(dev).manual_seed(9306))
+    n = (1 << 31) + 77
+    reps = 1 << 11
+    A = torch.empty(n, 6, dtype=torch.float32, device=dev)
+    w = torch.empty(n, 3, dtype=torch.float32, device=dev)
+    A[: 1 << 31].view(reps, base_n, 6).copy_(base.unsqueeze(0).expand(reps, base_n, 6))
+    w[: 1 << 31].view(reps, base_n, 3).copy_(wb.unsqueeze(0).expand(reps, base_n, 3))
+    A[1 << 31:] = tail
+    w[1 << 31:] = wt
+    lb, gb = eig3.eigvals_vjp(base, wb, precision="f32c")
+    lt, gt = eig3.eigvals_vjp(tail, wt, precision="f32c")
+    lam, g = eig3.eigvals_vjp(A, w, precision="f32c")
+    torch.cuda.synchronize()
+    assert torch.equal(lam[: 1 << 31].view(reps, base_n, 3), lb.unsqueeze(0).expand(reps, base_n, 3))
+    assert torch.equal(g[: 1 << 31].view(reps, base_n, 6), gb.unsqueeze(0).expand(reps, base_n, 6))
+    assert torch.equal(lam[1 << 31:], lt) and torch.equal(g[1 << 31:], gt)
+    assert torch.equal(lb, eig3.eigvals(base, precision="f32c"))
