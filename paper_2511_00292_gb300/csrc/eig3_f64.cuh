@@ -316,11 +316,13 @@ struct ShareS {
 //   r2  = M01 X - M02 (M02 M21),              X = M01 M12 - M02 d2
 //   r3  = M01 (M21 d1 - M01 M20) + M21 (M02 M21)
 //   r4  = M12 (M02 d0 + M01 M12) - M02 (M02 M10)
-//   r5  = M01 Y + M12 (M02 M21),              Y = M12 d1 - M02 M10
-//   r6  = M02 (M21 d0 - M01 M20) + M21 (M01 M12)
-//   r7  = M10 X - M12 (M02 M20)
+//   r5  = r12 + r13,  r6 = r11 - r10,  r7 = r8 - r9   (identities for any M:
+//         the d0 d2, d1 d2 and d0 d1 terms cancel, d0 + d2 = d1, d1 - d2 = d0,
+//         d1 - d0 = d2; each is one addition of two computed r's, whose
+//         rounding errors, like those of the direct sums, are units of u on
+//         terms of size |M|^3)
 //   r8  = d1 (M12 d0 - M02 M10) + M12 (M01 M10 - M12 M21)
-//   r9  = d0 Y + M12 (M02 M20 - M12 M21)
+//   r9  = d0 Y + M12 (M02 M20 - M12 M21),     Y = M12 d1 - M02 M10
 //   r10 = M01 (d1 d2 + M02 M20 - M01 M10) + d2 (M02 M21)
 //   r11 = M01 (d1 d2 + M12 M21 - M01 M10) + d1 (M02 M21)
 //   r12 = M02 (M12 M21 - M02 M20 - d0 d2) + d0 (M01 M12)
@@ -350,15 +352,18 @@ __device__ __forceinline__ Dx dx13(double M01, double M02, double M10, double M1
   r.r2 = fma(M01, X, -(M02 * m0221));
   r.r3 = fma(M01, fma(M21, s.d1, -m0120), M21 * m0221);
   r.r4 = fma(M12, fma(M02, s.d0, m0112), -(M02 * m0210));
-  r.r5 = fma(M01, Y, M12 * m0221);
-  r.r6 = fma(M02, fma(M21, s.d0, -m0120), M21 * m0112);
-  r.r7 = fma(M10, X, -(M12 * s.p02));
   r.r8 = fma(s.d1, fma(M12, s.d0, -m0210), M12 * s.e8);
   r.r9 = fma(s.d0, Y, M12 * s.e9);
   r.r10 = fma(M01, s.q10, s.d2 * m0221);
   r.r11 = fma(M01, s.q11, s.d1 * m0221);
   r.r12 = fma(M02, s.q12, s.d0 * m0112);
   r.r13 = fma(M02, s.q13, s.d2 * m0112);
+  // r5 = r12 + r13, r6 = r11 - r10, r7 = r8 - r9 for any M: the terms with
+  // d0 d2, d1 d2 and d0 d1 cancel, and the diagonal differences satisfy
+  // d0 + d2 = d1, d1 - d2 = d0, d1 - d0 = d2
+  r.r5 = r.r12 + r.r13;
+  r.r6 = r.r11 - r.r10;
+  r.r7 = r.r8 - r.r9;
   r.m0221 = m0221;
   return r;
 }
@@ -459,15 +464,17 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6], ShareS *x =
   const double offdiag = 2.0 * (ab * c);
   o.J3 = fma(fma(t1, fma(t2, tn * kInv9, fac), t2 * fbc), kInv3, offdiag);
   if (x) *x = ShareS{t1, t2, tn, a, b, c, aa, bb, cc, ab, ac, bc};
-  const double r2 = fma(a, fma(-b, d2, ac), -(b * bc));
-  const double r3 = fma(a, fma(c, d1, -ab), c * bc);
-  const double r4 = fma(c, fma(b, d0, ac), -(b * ab));
   const double r8 = fma(d1, fma(c, d0, -ab), c * fac);
   const double r9 = fma(d0, fma(c, d1, -ab), c * fbc);
   const double r10 = fma(a, fma(d1, d2, fba), d2 * bc);
   const double r11 = fma(a, fma(d1, d2, -fac), d1 * bc);
   const double r12 = fma(b, fma(-d0, d2, -fbc), d0 * ac);
   const double r13 = fma(b, fma(d0, d2, fba), d2 * ac);
+  // r2 = r8 - r9, r3 = r12 + r13, r4 = r11 - r10: the identities of dx13 (the
+  // diagonal differences satisfy d1 - d0 = d2, d0 + d2 = d1, d1 - d2 = d0)
+  const double r2 = r8 - r9;
+  const double r3 = r12 + r13;
+  const double r4 = r11 - r10;
   const double r14 = fma(d0, fma(d1, d2, -aa), fma(d1, bb, -(d2 * cc)));
   // 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2 as one FMA chain, the
   // weight 2 applied on the integer pipe (times_pow2)

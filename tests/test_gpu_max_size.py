@@ -66,6 +66,7 @@ def test_fused_beyond_2_31_rows(eig3):
     compensated binary32 half: eigenvalues equal eigvals' and every gradient
     row equals the small-batch result for the same matrix and weights."""
     dev = torch.device("cuda:0")
+    torch.cuda.empty_cache()  # the previous test's batch, still held by the allocator
     free, _ = torch.cuda.mem_get_info(dev)
     if free < 175e9:
         pytest.skip("needs about 175 GB of free device memory")
