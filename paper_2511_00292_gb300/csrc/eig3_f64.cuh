@@ -101,6 +101,16 @@ __device__ __forceinline__ double widen_scaled(float f, int s) {
   return ((b & 0x7f800000) == 0) ? 0.0 : __hiloint2double((b >> 3) + ((896 + s) << 20), b << 29);
 }
 
+// A double from its two 32-bit words through an opaque move.  Exponent
+// arithmetic done on the words (x 2^k for a k the code knows is in range)
+// would otherwise be recognised by the compiler as a multiplication by a
+// power of two and issued on the FP64 pipe, in some kernels and not others.
+__device__ __forceinline__ double from_words(int hi, int lo) {
+  double r;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+
 // Square root and reciprocal from binary32 seeds, corrected by a truncated
 // binomial series in binary64.  The correction is a handful of FMAs on the
 // FP64 pipe; the seed, the exponent handling and the special cases run on the
@@ -126,7 +136,7 @@ __device__ __forceinline__ double sqrt_nonneg_split(double x, int &k) {
   const int hi = __double2hiint(x);
   const int E = (hi >> 20) & 0x7ff;
   const int kk = (E - 1023) >> 1;
-  const double xs = __hiloint2double(hi - (kk << 21), __double2loint(x));
+  const double xs = from_words(hi - (kk << 21), __double2loint(x));
   float y0 = rsqrt_seed((float)C * seed_float(xs));
   if (C == 3) y0 = __int_as_float(__float_as_int(y0) & ~3);
   const double g = xs * widen((float)C * y0);
@@ -141,7 +151,7 @@ template <int C = 1>
 __device__ __forceinline__ double sqrt_nonneg(double x) {
   int k;
   const double s = sqrt_nonneg_split<C>(x, k);
-  return __hiloint2double(__double2hiint(s) + (k << 20), __double2loint(s));
+  return from_words(__double2hiint(s) + (k << 20), __double2loint(s));
 }
 
 // 1/x for positive normal x: with x = 2^k x', x' in [1, 2), the binary32
@@ -150,11 +160,11 @@ __device__ __forceinline__ double sqrt_nonneg(double x) {
 __device__ __forceinline__ double recip_pos(double x) {
   const int hi = __double2hiint(x);
   const int k = ((hi >> 20) & 0x7ff) - 1023;
-  const double xs = __hiloint2double(hi - (k << 20), __double2loint(x));
+  const double xs = from_words(hi - (k << 20), __double2loint(x));
   const double c0 = widen(rcp_seed(seed_float(xs)));
   const double e = fma(-xs, c0, 1.0);
   const double c = fma(c0, fma(e, e, e), c0);
-  return __hiloint2double(__double2hiint(c) - (k << 20), __double2loint(c));
+  return from_words(__double2hiint(c) - (k << 20), __double2loint(c));
 }
 
 // 1/(3x) for a positive normal x, as recip_pos: the binary32 seed of
@@ -164,13 +174,13 @@ __device__ __forceinline__ double recip_pos(double x) {
 __device__ __forceinline__ double recip3_pos(double x) {
   const int hi = __double2hiint(x);
   const int k = ((hi >> 20) & 0x7ff) - 1023;
-  const double xs = __hiloint2double(hi - (k << 20), __double2loint(x));
+  const double xs = from_words(hi - (k << 20), __double2loint(x));
   const float cf =
       __int_as_float(__float_as_int(rcp_seed(seed_float(xs)) * (1.0f / 3.0f)) & ~3);
   const double c0 = widen(cf);
   const double e = fma(-xs, widen(3.0f * cf), 1.0);
   const double c = fma(c0, fma(e, e, e), c0);
-  return __hiloint2double(__double2hiint(c) - (k << 20), __double2loint(c));
+  return from_words(__double2hiint(c) - (k << 20), __double2loint(c));
 }
 
 // x 2^k by adding k to the exponent field (integer pipe): exact for normal x
@@ -235,15 +245,16 @@ __device__ __forceinline__ double scale2k(double x, int k) {
     m = (mag & 0xfffffffffffffull) | 0x10000000000000ull;
   }
   const int ne = E + k;
-  if (ne >= 0x7ff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
-  if (ne >= 1)
-    return __longlong_as_double(
-        (long long)(sign | ((unsigned long long)ne << 52) | (m & 0xfffffffffffffull)));
+  if (ne >= 0x7ff) return from_words((int)((sign | 0x7ff0000000000000ull) >> 32), 0);
+  if (ne >= 1) {
+    const unsigned long long r = sign | ((unsigned long long)ne << 52) | (m & 0xfffffffffffffull);
+    return from_words((int)(r >> 32), (int)(unsigned)r);
+  }
   const int sh = 1 - ne;  // >= 1: the result is subnormal (or rounds up to 2^-1022)
-  if (sh > 54) return __longlong_as_double((long long)sign);
+  if (sh > 54) return from_words((int)(sign >> 32), 0);
   const unsigned long long q = m >> sh, rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
   const unsigned long long r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
-  return __longlong_as_double((long long)(sign | r));
+  return from_words((int)((sign | r) >> 32), (int)(unsigned)(sign | r));
 }
 
 // |x| by clearing the sign bit (integer pipe, in PTX for the same reason: a

@@ -25,6 +25,10 @@ PRELUDE = r"""
 static inline long long __double_as_longlong(double x) { long long b; memcpy(&b, &x, 8); return b; }
 static inline double __longlong_as_double(long long b) { double x; memcpy(&x, &b, 8); return x; }
 static inline int __clzll(long long x) { return x == 0 ? 64 : __builtin_clzll((unsigned long long)x); }
+static inline double from_words(int hi, int lo) {
+  const unsigned long long b = ((unsigned long long)(unsigned)hi << 32) | (unsigned)lo;
+  double x; memcpy(&x, &b, 8); return x;
+}
 """
 
 
