@@ -166,7 +166,8 @@ __device__ __forceinline__ Diag diag_parts(float a00, float a11, float a22) {
 //   Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2,
 // two ways.  disc_sym_compensated keeps it a Sum2 state (the invariants
 // output, accurate at u32^2).  disc_sym_rounded serves the eigenvalue
-// kernels, which round Delta to binary32 before the angle: every term is
+// kernels of precision EIG3_PREC_F32_COMP_A64 (the default compensated
+// eigenvalues take invariants_sym_eig below): every term is
 // non-negative, so nothing cancels and no compensation is needed -- each
 // (s + c)^2 is rounded once (sq1) and the terms are summed in a tree, a
 // relative error of a few units of binary32 against the 14 compensated
@@ -208,8 +209,8 @@ __device__ __forceinline__ Sum disc_sym_rounded(Sum r2, Sum r3, Sum r4, Sum r8, 
 //   r14 = d0d1d2 - aa d0 + bb d1 - cc d2
 //   Delta = 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2.
 // ---------------------------------------------------------------------------
-// EIG: for the eigenvalue kernels (Delta by disc_sym_rounded); otherwise the
-// invariants output (disc_sym_compensated).
+// EIG: for the EIG3_PREC_F32_COMP_A64 eigenvalues (Delta by disc_sym_rounded);
+// otherwise the invariants output (disc_sym_compensated).
 template <bool EIG = false>
 __device__ __forceinline__ InvC invariants_sym_c(float a00, float a11, float a22, float c0,
                                                  float b0, float a0) {
