@@ -42,9 +42,15 @@
  *  EIG3_F32 + EIG3_PREC_F32_COMP   binary32 in, binary32 compensated arithmetic
  *                                  (error-free TwoSum/TwoProduct transformations,
  *                                  per-matrix power-of-two scaling of the
- *                                  deviatoric part), binary32 out.  No binary64
- *                                  arithmetic on this path except the binary64
- *                                  invariants output of eig3_invariants.
+ *                                  deviatoric part), binary32 out.  The
+ *                                  invariants output is accumulated by Sum2
+ *                                  (accurate at u32^2); the eigenvalues of
+ *                                  symmetric input take the invariants from
+ *                                  sums on a fixed grid, accurate to the
+ *                                  absolute level the triple angle needs.  No
+ *                                  binary64 arithmetic on this path except the
+ *                                  binary64 invariants output of
+ *                                  eig3_invariants.
  *  EIG3_F32 + EIG3_PREC_F32_COMP_A64
  *                                  as EIG3_PREC_F32_COMP, except that the final
  *                                  combination of the compensated Delta and
