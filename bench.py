@@ -758,7 +758,7 @@ def measure_paths(eig3, W, dev, stream, steps, S, G, step_fns, lam, grad):
     return paths
 
 
-def measure_e2e(eig3, S, G, dev, stream, steps, shift=0):
+def measure_e2e(eig3, S, G, dev, stream, steps, shift=0, chunk=1 << 21):
     """The same step on host-resident data through the public API
     (paper_2511_00292_gb300.host.HostPipeline): the matrices and loss weights
     start in pinned host memory and the eigenvalues and gradients end there;
@@ -777,7 +777,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0):
     ogG = pinned_empty(hG.shape, hG.dtype)
     h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
     d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
-    pipe = HostPipeline(dev, chunk=1 << 21, depth=3)
+    pipe = HostPipeline(dev, chunk=chunk, depth=3)
 
     graph = pipe.capture([(hS, hwS, olS, ogS, None, "f32c"), (hG, hwG, olG, ogG, None, "f64")])
 
@@ -835,7 +835,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0):
     return {"value": (mS + mG) / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
             "matrices_per_gpu": mS + mG,
             "mode": "pinned host buffers (host.pinned_empty: huge-page mappings registered "
-                    "with CUDA), chunks of 2^21 streamed through 3 device slots "
+                    f"with CUDA), chunks of 2^{chunk.bit_length() - 1} streamed through 3 device slots "
                     "(H2D / kernels / D2H on 3 streams), captured once as a CUDA graph",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
             "results_match_device": ok,
