@@ -765,7 +765,8 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0, chunk=1 << 21):
     every host-to-device and device-to-host copy is inside the timed region,
     overlapped with the kernels chunk by chunk on separate streams.  `shift`
     halves the batch that many times (host memory shared by several ranks)."""
-    from paper_2511_00292_gb300.host import HostPipeline, pinned_copy, pinned_empty
+    from paper_2511_00292_gb300.host import (HostPipeline, huge_page_fraction, pinned_copy,
+                                             pinned_empty)
     mS, mG = S.n >> shift, G.n >> shift
     hS = pinned_copy(S.A[:mS])
     hG = pinned_copy(G.A[:mG])
@@ -775,6 +776,25 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0, chunk=1 << 21):
     olG = pinned_empty((mG, 3), torch.float64)
     ogS = pinned_empty(hS.shape, hS.dtype)
     ogG = pinned_empty(hG.shape, hG.dtype)
+    # A buffer the kernel left without huge pages copies at a few GB/s and
+    # holds the whole step back (measured: the first host copy of a fresh
+    # process, 3 GiB, 0 % huge pages, 3.8 GB/s); such a buffer is made again,
+    # the later ones having come out fully backed
+    remade = []
+
+    def backed(name, t, fill):
+        if huge_page_fraction(t) >= 0.9:
+            return t
+        remade.append(name)
+        return pinned_copy(fill) if fill is not None else pinned_empty(t.shape, t.dtype)
+
+    hS = backed("A_sym6", hS, S.A[:mS])
+    hG = backed("A_general9", hG, G.A[:mG])
+    hwS = backed("w_sym6", hwS, S.extra["w"][:mS])
+    hwG = backed("w_general9", hwG, G.extra["w"][:mG])
+    olS, olG = backed("lam_sym6", olS, None), backed("lam_general9", olG, None)
+    ogS, ogG = backed("grad_sym6", ogS, None), backed("grad_general9", ogG, None)
+    huge = min(huge_page_fraction(t) for t in (hS, hG, hwS, hwG, olS, olG, ogS, ogG))
     h2d = sum(t.numel() * t.element_size() for t in (hS, hG, hwS, hwG))
     d2h = sum(t.numel() * t.element_size() for t in (olS, olG, ogS, ogG))
     pipe = HostPipeline(dev, chunk=chunk, depth=3)
@@ -838,6 +858,7 @@ def measure_e2e(eig3, S, G, dev, stream, steps, shift=0, chunk=1 << 21):
                     f"with CUDA), chunks of 2^{chunk.bit_length() - 1} streamed through 3 device slots "
                     "(H2D / kernels / D2H on 3 streams), captured once as a CUDA graph",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
+            "host_huge_page_fraction_min": huge, "host_buffers_remade": remade,
             "results_match_device": ok,
             "copy_roofline": {"both_directions_gbs_each": each_gbs, "floor_ms": floor_ms,
                               "frac": floor_ms / ms},

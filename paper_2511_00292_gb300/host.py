@@ -26,6 +26,25 @@ import torch
 from . import eigvals, eigvals_backward, eigvals_vjp, layout_of
 
 
+def _huge_backed_bytes(lo: int, hi: int) -> int:
+    """Bytes of [lo, hi) that /proc/self/smaps reports as backed by anonymous
+    huge pages (summed over the mappings overlapping the range)."""
+    total = 0
+    inside = False
+    try:
+        with open("/proc/self/smaps") as f:
+            for line in f:
+                head = line.split(None, 1)[0]
+                if "-" in head and not head.endswith(":"):
+                    a, b = head.split("-")
+                    inside = int(a, 16) < hi and int(b, 16) > lo
+                elif inside and head == "AnonHugePages:":
+                    total += int(line.split()[1]) * 1024
+    except OSError:
+        return 0
+    return total
+
+
 class _PinnedMap(mmap.mmap):
     """Page-locked host memory behind `pinned_empty`: an anonymous private
     mapping advised for transparent huge pages (MADV_HUGEPAGE) and registered
@@ -77,6 +96,15 @@ def pinned_empty(shape, dtype=torch.float64) -> torch.Tensor:
         return torch.empty(shape, dtype=dtype, pin_memory=True)
     region = _PinnedMap.create(nbytes)
     return torch.frombuffer(region, dtype=torch.uint8, count=nbytes).view(dtype).view(shape)
+
+
+def huge_page_fraction(t: torch.Tensor) -> float:
+    """The fraction of the host tensor t's bytes backed by transparent huge
+    pages (0 where the kernel does not report it)."""
+    nbytes = t.numel() * t.element_size()
+    if nbytes == 0:
+        return 1.0
+    return min(1.0, _huge_backed_bytes(t.data_ptr(), t.data_ptr() + nbytes) / nbytes)
 
 
 def pinned_copy(t: torch.Tensor) -> torch.Tensor:

@@ -72,3 +72,21 @@ def test_failed_registration_raises(monkeypatch):
         host.pinned_empty((64, 6), torch.float32)
     gc.collect()
     assert [c[0] for c in f.calls] == ["register"]  # nothing to unregister
+
+
+def test_huge_page_fraction_reads_smaps():
+    """The smaps reader finds the anonymous huge pages (or none) of a live
+    mapping without error; a range outside every mapping counts 0; an empty
+    tensor counts as fully backed."""
+    m = mmap.mmap(-1, 1 << 20, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    import ctypes
+    buf = (ctypes.c_char * (1 << 20)).from_buffer(m)
+    a = ctypes.addressof(buf)
+    buf[0] = b"x"
+    assert host._huge_backed_bytes(a, a + (1 << 20)) >= 0
+    assert host._huge_backed_bytes(8, 16) == 0
+    del buf
+    m.close()
+    t = torch.zeros(1000)
+    assert 0.0 <= host.huge_page_fraction(t) <= 1.0
+    assert host.huge_page_fraction(torch.zeros(0)) == 1.0
