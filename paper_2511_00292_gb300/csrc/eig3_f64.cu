@@ -1,9 +1,10 @@
 // eig3_f64.cu -- binary64 kernels: invariants, eigenvalues (+ adjoint inputs,
-// + statistics) and the adjoint, for the general 9-entry and symmetric
-// 6-entry layouts with binary64 or binary32 storage.
+// + statistics), the adjoint, the fused forward + vector-Jacobian product and
+// the eigenprojectors, for the general 9-entry and symmetric 6-entry layouts
+// with binary64 or binary32 storage.
 //
-// One thread per matrix.  The eigenvalue kernel's warps walk the batch in
-// tiles of 32 rows each (for_each_row_warp: no block barrier); the other
+// One thread per matrix.  The eigenvalue and fused kernels' warps walk the
+// batch in tiles of 32 rows each (for_each_row_warp: no block barrier); the other
 // kernels' blocks of 256 threads in tiles of 256 rows (for_each_row /
 // for_each_tile); either way the grid is sized to fill every SM and the input
 // rows of the next tile are copied into shared memory with asynchronous

@@ -8,7 +8,8 @@
 // Algorithm 5.  The numerical structure of the paper is kept: the diagonal
 // enters only through the differences d0, d1, d2, every r_i of Algorithm 5
 // is a sum of products of small factors, and the discriminant is the weighted
-// sum of products u_i v_i.  Only the grouping of the products changes, which
+// sum of products u_i v_i.  Only the grouping of the products changes (and
+// three r_i of dx(M) come from exact identities between the others), which
 // moves rounding errors by a few units in the last place.
 #pragma once
 
