@@ -651,11 +651,15 @@ __device__ __forceinline__ AdjC adjoint_c(float r, float sigma1, float sigma2, f
   const float g23 = k2 * sigma2;
   const float g13 = k2 * (sigma1 + sigma2);
   const bool z1 = g12 == 0.0f, z2 = g23 == 0.0f;
-  // an exactly coalesced pair takes the mean of its two weights
-  const float D12 = z1 ? 0.0f : ((z2 ? 0.5f * (g2 + g3) : g2) - g1) / g12;
-  const float D23 = z2 ? 0.0f : (g3 - (z1 ? 0.5f * (g1 + g2) : g2)) / g23;
+  // an exactly coalesced pair takes the mean of its two weights.  The
+  // divisions are the two-instruction approximate quotient (within 2 ulp):
+  // g13 = (2/sqrt3) cos(psi - pi/6) >= 1, and g12, g23 are either exactly 0
+  // (guarded) or above 2^-75 (the scaled Delta's smallest positive value
+  // gives an angle of that order), so every divisor is a normal number
+  const float D12 = z1 ? 0.0f : __fdividef((z2 ? 0.5f * (g2 + g3) : g2) - g1, g12);
+  const float D23 = z2 ? 0.0f : __fdividef(g3 - (z1 ? 0.5f * (g1 + g2) : g2), g23);
   AdjC o;
-  o.aJ3r2 = (g13 != 0.0f) ? (D23 - D12) / g13 : 0.0f;
+  o.aJ3r2 = (g13 != 0.0f) ? __fdividef(D23 - D12, g13) : 0.0f;
   o.aJ2r = fmaf(-0.38490017945975050967f * fmaf(2.0f, sigma1, sigma2), o.aJ3r2, D23);
   o.aI1 = ((g1 + g2) + g3) * (1.0f / 3.0f);
   // r below the normal range counts as a triple eigenvalue
@@ -672,9 +676,10 @@ struct Adj3C {
 __device__ __forceinline__ Adj3C adjoint_units_c(float r, float sigma1, float sigma2) {
   const float h = 0.86602540378443864676f;  // sqrt3 / 2
   const bool z1 = sigma1 == 0.0f, z2 = sigma2 == 0.0f;
-  const float X12 = z1 ? 0.0f : h / sigma1;
-  const float X23 = z2 ? 0.0f : h / sigma2;
-  const float X13 = h / (sigma1 + sigma2);
+  // approximate quotients as in adjoint_c: every divisor is a normal number
+  const float X12 = z1 ? 0.0f : __fdividef(h, sigma1);
+  const float X23 = z2 ? 0.0f : __fdividef(h, sigma2);
+  const float X13 = __fdividef(h, sigma1 + sigma2);
   const float c = -0.38490017945975050967f * fmaf(2.0f, sigma1, sigma2);
   Adj3C o;
 #pragma unroll

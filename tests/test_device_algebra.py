@@ -561,6 +561,7 @@ ENV_C = dict(
     gsum=val, gdiff=lambda x, y: V(val(x) - val(y)),
     round1=val, __fmul_rn=lambda a, b: val(a) * val(b), __fadd_rn=lambda a, b: val(a) + val(b),
     __fsub_rn=lambda a, b: val(a) - val(b), __fmaf_rn=lambda a, b, c: val(a) * val(b) + val(c),
+    __fdividef=lambda a, b: val(a) / val(b),
     fmaf=lambda a, b, c: a * b + c, det2=lambda a, d, b, c: a * d - b * c,
     pow2_from_field=lambda f: 1, **EXACT)
 # decimal constants of the binary32 source and the exact values they round
