@@ -56,21 +56,24 @@ WORKLOAD = ("mixed fwd+bwd, 2^28 matrices/GPU: 2^27 symmetric 6-entry FP32 (comp
 # launch as in the timed step): thread-level instructions on the FP64 pipe
 # (active lanes only) and the warp-level count times 32 (what occupies the
 # pipe, idle lanes included), of which DFMA / DMUL / DADD, and DRAM bytes read
-# + written.  They describe the kernel source whose
+# + written; int_dmul is the number of binary64 products each matrix forms on
+# the integer pipes (dmul call sites on the kernel's path, one execution each;
+# tests/test_bench_helpers.py counts them in the source).  They describe the
+# kernel source whose
 # hash is recorded; when the source changes they are reported as stale and
 # every figure derived from them as null.
 KERNEL_COUNTERS = {
     "vjp_f64_general9": {
-        "source_md5": "b8efe72de6deabb3195234913635756b",
-        "fp64_pipe_inst": 205.02, "fp64_warp_inst_x32": 205.50,
-        "dfma": 104.01, "dmul": 73.00, "dadd": 28.01,
-        "dram_bytes": (402.717440e6 + 354.974720e6) / 4194304,
+        "source_md5": "86adad632b0634133c0aeb83dce1e6d7",
+        "fp64_pipe_inst": 145.02, "fp64_warp_inst_x32": 145.50,
+        "dfma": 105.01, "dmul": 5.00, "dadd": 35.01, "int_dmul": 68,
+        "dram_bytes": (404.477952e6 + 351.434496e6) / 4194304,
     },
     "fwd_f64_general9": {
-        "source_md5": "a81b13286d27b38816e33cb31513140a",
-        "fp64_pipe_inst": 155.00, "fp64_warp_inst_x32": 155.00,
-        "dfma": 79.00, "dmul": 54.00, "dadd": 22.00,
-        "dram_bytes": (302.070528e6 + 191.976960e6) / 4194304,
+        "source_md5": "2d732d8b39ce21f05ded55ca3f6fd525",
+        "fp64_pipe_inst": 109.00, "fp64_warp_inst_x32": 109.00,
+        "dfma": 79.00, "dmul": 7.00, "dadd": 23.00, "int_dmul": 47,
+        "dram_bytes": (302.076416e6 + 189.888000e6) / 4194304,
     },
 }
 # What each hash covers: the headers whole and, of eig3_f64.cu (which holds
@@ -78,9 +81,9 @@ KERNEL_COUNTERS = {
 # helper of that file they use (tests/test_bench_helpers.py checks the list
 # against the kernel bodies).
 KERNEL_SOURCES = {
-    "vjp_f64_general9": ("eig3_f64.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
+    "vjp_f64_general9": ("eig3_f64.cuh", "eig3_dmul.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
                          ("eig3_f64.cu", ("k_eigvals_vjp", "vjp_launch4", "vjp_launch", "Width"))),
-    "fwd_f64_general9": ("eig3_f64.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
+    "fwd_f64_general9": ("eig3_f64.cuh", "eig3_dmul.cuh", "eig3_stats.cuh", "eig3_tile.cuh",
                          ("eig3_f64.cu", ("k_eigvals", "eig_launch4", "eig_launch", "store_aux",
                                           "invariants_of", "aligned16", "Width"))),
 }
@@ -387,44 +390,59 @@ def measure_fp_peaks(dev, stream):
         fp64 = max(one(kind, c, b, 256, 30.0) for kind in (0, 4, 5) for c in (2, 8)
                    for b in (1, 4))
         fp32 = max(one(3, c, b, 256, 30.0) for c in (8, 16) for b in (4, 8))
+        emul = max(one(8, c, b, 256, 30.0) for c in (4, 8) for b in (2, 4))
     return {"fp64_tinst_per_s": fp64, "fp64_tflops_measured": 2.0 * fp64,
             "fp32_tinst_per_s": fp32, "fp32_tflops_measured": 2.0 * fp32,
+            "int_dmul_tops_measured": emul,
             "fp64_loops": "DFMA chains alone and between integer or FFMA work, "
                           "2 or 8 chains per thread, 1 or 4 blocks of 256 per SM; best",
+            "int_dmul_loops": "binary64 multiplications on the integer pipes (the kernels' "
+                              "dmul), 4 or 8 chains per thread, 2 or 4 blocks of 256 per SM; "
+                              "best",
             "clocks": clocks.summary(), "runs": runs}
 
 
 def kernel_roofline(name, label, n, ms, fp, sm_mhz, sms, hbm_gbs):
-    """Roofline object of one binary64 kernel launch: the flop basis (counted
-    FP operations, FMA = 2, from its ncu counters) against the measured FP64
-    peak, with the FP64-pipe issue view and the nominal unit-count peak
-    beside it.  Null where the counters are stale."""
+    """Roofline object of one binary64 kernel launch on the flop basis: its
+    binary64 operations per matrix (FMA = 2), those on the FP64 pipe from its
+    ncu counters plus the multiplications it forms on the integer pipes
+    (dmul, counted from its source), against the two measured peaks added:
+    the DFMA loop's flop rate and the integer-pipe multiplication loop's rate.
+    Beside it: the same against the FP64 pipe's peak alone, the FP64-pipe
+    issue view and the nominal unit-count peak.  Null where the counters are
+    stale."""
     c = KERNEL_COUNTERS[name]
     fresh = c["source_md5"] is not None and kernel_source_md5(KERNEL_SOURCES[name]) == c[
         "source_md5"]
     t = ms * 1e-3
     nominal_inst = sms * FP64_LANES_PER_SM * sm_mhz * 1e6 / 1e12         # T inst/s
-    peak = fp["fp64_tflops_measured"]
+    peak = fp["fp64_tflops_measured"] + fp["int_dmul_tops_measured"]
     out = {"kernel": label, "bound": "alu", "unit": "TFLOP/s", "counters_fresh": fresh,
            "peak": peak,
-           "peak_source": f"measured in this run: fastest DFMA loop (libeig3_peaks), "
-                          f"{fp['fp64_tinst_per_s']:.4f} T DFMA/s",
+           "peak_source": f"measured in this run (libeig3_peaks): fastest DFMA loop, "
+                          f"{fp['fp64_tinst_per_s']:.4f} T DFMA/s x 2 flop, plus fastest "
+                          f"integer-pipe multiplication loop, "
+                          f"{fp['int_dmul_tops_measured']:.4f} T/s",
            "peak_nominal": 2.0 * nominal_inst,
-           "peak_nominal_source": f"{sms} SMs x {FP64_LANES_PER_SM} FP64 FMA lanes x "
-                                  f"{sm_mhz:.0f} MHz x 2 flop",
+           "peak_nominal_source": f"FP64 pipe alone: {sms} SMs x {FP64_LANES_PER_SM} FP64 FMA "
+                                  f"lanes x {sm_mhz:.0f} MHz x 2 flop",
            "fp64_tflops_measured": fp["fp64_tflops_measured"],
+           "int_dmul_tops_measured": fp["int_dmul_tops_measured"],
            "fp32_tflops_measured": fp["fp32_tflops_measured"],
            "ms": ms, "matrices": n, "G_matrices_per_s": n / t / 1e9}
     hbm = KERNEL_BYTES[name]
     out["hbm_view"] = {"bytes_per_matrix": hbm, "achieved_gbs": hbm * n / t / 1e9,
                        "peak_gbs": hbm_gbs, "frac": hbm * n / t / 1e9 / hbm_gbs}
     if not fresh:
-        out.update(achieved=None, frac=None, frac_vs_nominal=None, frac_issue=None, traffic=None)
+        out.update(achieved=None, frac=None, frac_vs_fp64_peak=None, frac_vs_nominal=None,
+                   frac_issue=None, traffic=None)
         return out
-    flop = 2 * c["dfma"] + c["dmul"] + c["dadd"]
+    pipe_flop = 2 * c["dfma"] + c["dmul"] + c["dadd"]
+    flop = pipe_flop + c["int_dmul"]
     achieved = flop * n / t / 1e12
     inst_rate = c["fp64_warp_inst_x32"] * n / t / 1e12      # pipe occupancy
     out.update(achieved=achieved, frac=achieved / peak,
+               frac_vs_fp64_peak=achieved / fp["fp64_tflops_measured"],
                frac_vs_nominal=achieved / (2.0 * nominal_inst),
                frac_issue=inst_rate / nominal_inst,
                frac_issue_vs_measured_loop=inst_rate / fp["fp64_tinst_per_s"],
@@ -432,8 +450,8 @@ def kernel_roofline(name, label, n, ms, fp, sm_mhz, sms, hbm_gbs):
                algorithmic_per_matrix={"flop": flop, "fp64_pipe_inst": c["fp64_pipe_inst"],
                                        "fp64_warp_inst_x32": c["fp64_warp_inst_x32"],
                                        "dfma": c["dfma"], "dmul": c["dmul"], "dadd": c["dadd"],
-                                       "hbm_bytes": hbm},
-               mix_ceiling=flop / (2.0 * c["fp64_warp_inst_x32"]))
+                                       "int_dmul": c["int_dmul"], "hbm_bytes": hbm},
+               mix_ceiling=pipe_flop / (2.0 * c["fp64_warp_inst_x32"]))
     return out
 
 
@@ -558,7 +576,7 @@ def run_ours(args):
     lit = ops["add"] + ops["mul"] + ops["div"]
     roofline_fwd["oracle_literal_ops_per_matrix"] = dict(ops, flop=lit)
     roofline_fwd["frac_oracle_literal_flop"] = lit * nG / (kern["fwd_f64_general9"] * 1e-3) / 1e12 \
-        / fp["fp64_tflops_measured"]
+        / roofline_fwd["peak"]
 
     # ---- the other workloads' paths (fwd, fwd+bwd, FP64 vs compensated FP32) ----
     paths = {}

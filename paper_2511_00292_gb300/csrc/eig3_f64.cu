@@ -129,7 +129,7 @@ __device__ __forceinline__ bool aligned16(const void *p) {
 }
 
 template <int LAYOUT, typename T, bool AUX, bool STATS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
     k_eigvals(const T *__restrict__ A, int64_t n, T *__restrict__ lam, T *__restrict__ aux,
               eig3_stats *__restrict__ stats) {
   constexpr int N = Width<LAYOUT>::N;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads)
 // The rows of A go through the warp's shared-memory tiles; the three weights
 // of a row are read directly (24 or 12 bytes, contiguous across the warp).
 template <int LAYOUT, typename T, bool LAM, bool STATS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
     k_eigvals_vjp(const T *__restrict__ A, const T *__restrict__ w, int64_t n,
                   T *__restrict__ lam, T *__restrict__ gA, eig3_stats *__restrict__ stats) {
   constexpr int N = Width<LAYOUT>::N;

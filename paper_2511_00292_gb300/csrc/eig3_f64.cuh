@@ -5,7 +5,8 @@
 // DFMA per SM per clock (64x below FP32): every DADD/DMUL/DFMA counts, so the
 // algorithms are evaluated with fused multiply-adds and with products shared
 // between the invariants, between dx(A) and dx(A^T), and between the terms of
-// Algorithm 5.  The numerical structure of the paper is kept: the diagonal
+// Algorithm 5, and many of the plain products are formed on the integer pipes
+// (dmul, bit-identical to the FP64 multiplication) to share the work.  The numerical structure of the paper is kept: the diagonal
 // enters only through the differences d0, d1, d2, every r_i of Algorithm 5
 // is a sum of products of small factors, and the discriminant is the weighted
 // sum of products u_i v_i.  Only the grouping of the products changes (and
@@ -16,7 +17,15 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "eig3_dmul.cuh"
+
 namespace eig3 {
+
+// A binary64 product on the integer pipes (softfp::mul_rn_int: the same bits
+// as x * y).  The kernels are bound by the FP64 pipe while their integer
+// pipes are nearly idle, so the products of the invariants (Algorithms 2, 4
+// and 5) are formed here and the FP64 pipe keeps the FMAs and the rest.
+__device__ __forceinline__ double dmul(double x, double y) { return softfp::mul_rn_int(x, y); }
 
 // Constants (binary64 nearest values).
 constexpr double kInv3 = 0.333333333333333314829616256247390992939472198486328125;
@@ -357,19 +366,19 @@ struct Dx {
 __device__ __forceinline__ Dx dx13(double M01, double M02, double M10, double M12, double M20,
                                    double M21, double m0112, double m0210, const DxShared &s) {
   Dx r;
-  const double m0221 = M02 * M21;
-  const double m0120 = M01 * M20;
+  const double m0221 = dmul(M02, M21);
+  const double m0120 = dmul(M01, M20);
   const double X = fma(-M02, s.d2, m0112);
   const double Y = fma(M12, s.d1, -m0210);
-  r.r2 = fma(M01, X, -(M02 * m0221));
-  r.r3 = fma(M01, fma(M21, s.d1, -m0120), M21 * m0221);
-  r.r4 = fma(M12, fma(M02, s.d0, m0112), -(M02 * m0210));
-  r.r8 = fma(s.d1, fma(M12, s.d0, -m0210), M12 * s.e8);
-  r.r9 = fma(s.d0, Y, M12 * s.e9);
-  r.r10 = fma(M01, s.q10, s.d2 * m0221);
-  r.r11 = fma(M01, s.q11, s.d1 * m0221);
-  r.r12 = fma(M02, s.q12, s.d0 * m0112);
-  r.r13 = fma(M02, s.q13, s.d2 * m0112);
+  r.r2 = fma(M01, X, -dmul(M02, m0221));
+  r.r3 = fma(M01, fma(M21, s.d1, -m0120), dmul(M21, m0221));
+  r.r4 = fma(M12, fma(M02, s.d0, m0112), -dmul(M02, m0210));
+  r.r8 = fma(s.d1, fma(M12, s.d0, -m0210), dmul(M12, s.e8));
+  r.r9 = fma(s.d0, Y, dmul(M12, s.e9));
+  r.r10 = fma(M01, s.q10, dmul(s.d2, m0221));
+  r.r11 = fma(M01, s.q11, dmul(s.d1, m0221));
+  r.r12 = fma(M02, s.q12, dmul(s.d0, m0112));
+  r.r13 = fma(M02, s.q13, dmul(s.d2, m0112));
   // r5 = r12 + r13, r6 = r11 - r10, r7 = r8 - r9 for any M: the terms with
   // d0 d2, d1 d2 and d0 d1 cancel, and the diagonal differences satisfy
   // d0 + d2 = d1, d1 - d2 = d0, d1 - d0 = d2
@@ -395,11 +404,11 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9], ShareG *
   s.d1 = sv[1];
   s.d2 = sv[2];
   const double a01 = sv[3], a02 = sv[4], a10 = sv[5], a12 = sv[6], a20 = sv[7], a21 = sv[8];
-  s.p01 = a01 * a10;
-  s.p02 = a02 * a20;
-  s.p12 = a12 * a21;
+  s.p01 = dmul(a01, a10);
+  s.p02 = dmul(a02, a20);
+  s.p12 = dmul(a12, a21);
   // Algorithm 2: diag/6 + offdiag
-  o.J2 = fma(fma(s.d0, s.d0, fma(s.d1, s.d1, s.d2 * s.d2)), kInv6, (s.p01 + s.p02) + s.p12);
+  o.J2 = fma(fma(s.d0, s.d0, fma(s.d1, s.d1, dmul(s.d2, s.d2))), kInv6, (s.p01 + s.p02) + s.p12);
   // Algorithm 5's differences of the paired products, shared with J3:
   // e8 = A01 A10 - A12 A21, e9 = A02 A20 - A12 A21
   s.e8 = s.p01 - s.p12;
@@ -413,10 +422,10 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9], ShareG *
   const double tn = s.d0 + s.d1;
   // A01 A12 A20 + A02 A10 A21; the same two triple products give r1 of
   // Algorithm 5 for A, and r1 for A^T is its negative (A10 A21 A02 - A20 A01 A12)
-  const double m0112 = a01 * a12, m0210 = a02 * a10;
-  const double q = m0210 * a21;
+  const double m0112 = dmul(a01, a12), m0210 = dmul(a02, a10);
+  const double q = dmul(m0210, a21);
   const double offdiag = fma(m0112, a20, q);
-  o.J3 = fma(fma(t1, fma(t2, tn * kInv9, s.e8), t2 * s.e9), kInv3, offdiag);
+  o.J3 = fma(fma(t1, fma(t2, dmul(tn, kInv9), s.e8), dmul(t2, s.e9)), kInv3, offdiag);
   // Algorithm 5 (reading R1 for r10).  The bracketed sums of r10 .. r14 are
   // single FMAs (d1 d2 + (A02 A20 - A01 A10) and so on); p12 - p01 = -e8 and
   // p12 - p02 = -e9 exactly.
@@ -425,9 +434,9 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9], ShareG *
   s.q11 = fma(s.d1, s.d2, -s.e8);
   s.q12 = fma(-s.d0, s.d2, -s.e9);
   s.q13 = fma(s.d0, s.d2, f0201);
-  const double r14 = fma(s.d0, fma(s.d1, s.d2, -s.p01), fma(s.d1, s.p02, -(s.d2 * s.p12)));
+  const double r14 = fma(s.d0, fma(s.d1, s.d2, -s.p01), fma(s.d1, s.p02, -dmul(s.d2, s.p12)));
   const double r1 = fma(m0112, a20, -q);
-  const double m1021 = a10 * a21, m2001 = a20 * a01;
+  const double m1021 = dmul(a10, a21), m2001 = dmul(a20, a01);
   const Dx u = dx13(a01, a02, a10, a12, a20, a21, m0112, m0210, s);
   const Dx v = dx13(a10, a20, a01, a21, a02, a12, m1021, m2001, s);
   if (x) {
@@ -437,7 +446,7 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9], ShareG *
   // sum_i w_i u_i v_i, w = (9, 6, 6, 6, 8, 8, 8, 2, 2, 2, 2, 2, 2, 1), as one FMA
   // chain: w1 u1 v1 = 9 r1 (-r1), the power-of-two weights 2 and 8 applied to
   // u_i exactly on the integer pipe (times_pow2), the weight-6 group last
-  double acc = fma(-9.0 * r1, r1, r14 * r14);
+  double acc = fma(dmul(-9.0, r1), r1, dmul(r14, r14));
   acc = fma(times_pow2(u.r13, 1), v.r13, acc);
   acc = fma(times_pow2(u.r12, 1), v.r12, acc);
   acc = fma(times_pow2(u.r11, 1), v.r11, acc);
@@ -447,7 +456,7 @@ __device__ __forceinline__ Inv invariants_general(const double (&a)[9], ShareG *
   acc = fma(times_pow2(u.r7, 3), v.r7, acc);
   acc = fma(times_pow2(u.r6, 3), v.r6, acc);
   acc = fma(times_pow2(u.r5, 3), v.r5, acc);
-  o.D = fma(6.0, fma(u.r2, v.r2, fma(u.r3, v.r3, u.r4 * v.r4)), acc);
+  o.D = fma(6.0, fma(u.r2, v.r2, fma(u.r3, v.r3, dmul(u.r4, v.r4))), acc);
   return o;
 }
 
@@ -466,38 +475,38 @@ __device__ __forceinline__ Inv invariants_sym(const double (&s6)[6], ShareS *x =
   const double c = sv[3];  // A12
   const double b = sv[4];  // A02
   const double a = sv[5];  // A01
-  const double aa = a * a, bb = b * b, cc = c * c;
-  const double ab = a * b, ac = a * c, bc = b * c;
-  o.J2 = fma(fma(d0, d0, fma(d1, d1, d2 * d2)), kInv6, (aa + bb) + cc);
+  const double aa = dmul(a, a), bb = dmul(b, b), cc = dmul(c, c);
+  const double ab = dmul(a, b), ac = dmul(a, c), bc = dmul(b, c);
+  o.J2 = fma(fma(d0, d0, fma(d1, d1, dmul(d2, d2))), kInv6, (aa + bb) + cc);
   // Algorithm 4 as in the general case, (1/3) [t1 (e8 + t2 tn / 9) + t2 e9]
   // with e8 = aa - cc, e9 = bb - cc
   const double fba = bb - aa, fac = aa - cc, fbc = bb - cc;
   const double t1 = d1 + d2, t2 = d0 - d2, tn = d0 + d1;
-  const double offdiag = 2.0 * (ab * c);
-  o.J3 = fma(fma(t1, fma(t2, tn * kInv9, fac), t2 * fbc), kInv3, offdiag);
+  const double offdiag = scale2k(dmul(ab, c), 1);
+  o.J3 = fma(fma(t1, fma(t2, dmul(tn, kInv9), fac), dmul(t2, fbc)), kInv3, offdiag);
   if (x) *x = ShareS{t1, t2, tn, a, b, c, aa, bb, cc, ab, ac, bc};
-  const double r8 = fma(d1, fma(c, d0, -ab), c * fac);
-  const double r9 = fma(d0, fma(c, d1, -ab), c * fbc);
-  const double r10 = fma(a, fma(d1, d2, fba), d2 * bc);
-  const double r11 = fma(a, fma(d1, d2, -fac), d1 * bc);
-  const double r12 = fma(b, fma(-d0, d2, -fbc), d0 * ac);
-  const double r13 = fma(b, fma(d0, d2, fba), d2 * ac);
+  const double r8 = fma(d1, fma(c, d0, -ab), dmul(c, fac));
+  const double r9 = fma(d0, fma(c, d1, -ab), dmul(c, fbc));
+  const double r10 = fma(a, fma(d1, d2, fba), dmul(d2, bc));
+  const double r11 = fma(a, fma(d1, d2, -fac), dmul(d1, bc));
+  const double r12 = fma(b, fma(-d0, d2, -fbc), dmul(d0, ac));
+  const double r13 = fma(b, fma(d0, d2, fba), dmul(d2, ac));
   // r2 = r8 - r9, r3 = r12 + r13, r4 = r11 - r10: the identities of dx13 (the
   // diagonal differences satisfy d1 - d0 = d2, d0 + d2 = d1, d1 - d2 = d0)
   const double r2 = r8 - r9;
   const double r3 = r12 + r13;
   const double r4 = r11 - r10;
-  const double r14 = fma(d0, fma(d1, d2, -aa), fma(d1, bb, -(d2 * cc)));
+  const double r14 = fma(d0, fma(d1, d2, -aa), fma(d1, bb, -dmul(d2, cc)));
   // 14 (r2^2 + r3^2 + r4^2) + 2 (r8^2 + ... + r13^2) + r14^2 as one FMA chain, the
   // weight 2 applied on the integer pipe (times_pow2)
-  double acc = r14 * r14;
+  double acc = dmul(r14, r14);
   acc = fma(times_pow2(r13, 1), r13, acc);
   acc = fma(times_pow2(r12, 1), r12, acc);
   acc = fma(times_pow2(r11, 1), r11, acc);
   acc = fma(times_pow2(r10, 1), r10, acc);
   acc = fma(times_pow2(r9, 1), r9, acc);
   acc = fma(times_pow2(r8, 1), r8, acc);
-  o.D = fma(14.0, fma(r2, r2, fma(r3, r3, r4 * r4)), acc);
+  o.D = fma(14.0, fma(r2, r2, fma(r3, r3, dmul(r4, r4))), acc);
   return o;
 }
 
@@ -536,13 +545,13 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   float sf, cf;
   __sincosf(pf, &sf, &cf);
   const double c0 = widen(cf), s0 = widen(fmaxf(sf, 0.0f));
-  const double cc = c0 * c0, ss = s0 * s0;  // exact: 24-bit factors
+  const double cc = dmul(c0, c0), ss = dmul(s0, s0);  // exact: 24-bit factors
   // w0^3 = c0 (c0^2 - 3 s0^2) + i s0 (3 c0^2 - s0^2)
-  const double a3 = c0 * fma(-3.0, ss, cc);
-  const double b3 = s0 * fma(3.0, cc, -ss);
+  const double a3 = dmul(c0, fma(-3.0, ss, cc));
+  const double b3 = dmul(s0, fma(3.0, cc, -ss));
   // rho = z conj(w0^3); its argument is 3 eps (|3 eps| ~ 1e-6: arg = Im/Re to 1e-18)
-  const double re = fma(ax, a3, y * b3);
-  const double im = fma(y, a3, -(ax * b3));
+  const double re = fma(ax, a3, dmul(y, b3));
+  const double im = fma(y, a3, -dmul(ax, b3));
   // eps = im / (3 re): a binary32 seed rc0 of 1/(3 re) with 22 significant bits
   // (so that 3 rc0 is exact) and one Newton step, rc0 (1 + e), e = 1 - 3 re rc0
   const float rcf =
@@ -550,15 +559,15 @@ __device__ __forceinline__ void triple_angle_sines(double x, double y, double &s
   const double rc0 = widen_scaled(rcf, -s);
   const double e = fma(-re, widen_scaled(3.0f * rcf, -s), 1.0);
   // z = 0 (or both |x| and y subnormal): the angle is undetermined, keep phi = 0
-  const double eps = (h >= (1 << 20)) ? im * fma(rc0, e, rc0) : 0.0;
+  const double eps = (h >= (1 << 20)) ? dmul(im, fma(rc0, e, rc0)) : 0.0;
   // 1/|w0| to second order in eta0 = |w0|^2 - 1 (|eta0| ~ 1e-7), folded into
   // the rotation w~ = w0 e^{i eps} / |w0| with e^{i eps} = 1 - eps^2/2 + i eps
   const double eta0 = (cc - 1.0) + ss;
   const double f0 = fma(eta0, fma(eta0, 0.375, -0.5), 1.0);
-  const double ef = f0 * eps;
+  const double ef = dmul(f0, eps);
   const double cef = fma(-times_pow2(eps, -1), ef, f0);  // eps/2 on the integer pipe
-  const double ct = fma(c0, cef, -(s0 * ef));
-  const double st = nonneg(fma(s0, cef, c0 * ef));
+  const double ct = fma(c0, cef, -dmul(s0, ef));
+  const double st = nonneg(fma(s0, cef, dmul(c0, ef)));
   const double other = fma(kHalfSqrt3, ct, -times_pow2(st, -1));  // sin(pi/3 - psi~)
   // sign test on the bits: x = -0 goes with x < 0, as atan2(0, -0) = pi does
   const bool pos = __double2hiint(x) >= 0;
@@ -643,8 +652,8 @@ __device__ __forceinline__ Adj adjoint_scalars(double r, double sigma1, double s
   const bool rz = hr < (1 << 20);  // r = 0 or subnormal: a triple eigenvalue
   const int kr = min((hr >> 20) - 1023, 1022);
   const double m = rz ? 1.0 : scale2k(r, -kr);  // r 2^-kr on the integer pipe
-  const double s12 = s1 * s2;
-  const double P = s12 * s3;
+  const double s12 = dmul(s1, s2);
+  const double P = dmul(s12, s3);
   const double R = recip_pos(m * P);
   const double Rh = kHalfSqrt3 * R;
   double n12 = g2 - g1, n23 = g3 - g2;
@@ -688,8 +697,8 @@ __device__ __forceinline__ Adj3 adjoint_units(double r, double sigma1, double si
   const bool rz = hr < (1 << 20);
   const int kr = min((hr >> 20) - 1023, 1022);
   const double m = rz ? 1.0 : scale2k(r, -kr);  // r 2^-kr on the integer pipe
-  const double s12 = s1 * s2;
-  const double P = s12 * s3;
+  const double s12 = dmul(s1, s2);
+  const double P = dmul(s12, s3);
   const double R = recip_pos(m * P);
   const double Rh = kHalfSqrt3 * (m * R);
   const double X12 = (s2 * s3) * Rh;
@@ -877,7 +886,7 @@ __device__ __forceinline__ EigV eigvals_vjp_fwd(const Inv &v) {
   const double Dp = nonneg(v.D);
   o.m = sqrt_nonneg_split<3>(J2p, o.kr);
   triple_angle_sines(v.J3, sqrt_nonneg(Dp * kInv27), o.e.sigma1, o.e.sigma2);
-  o.kKm = kK * o.m;
+  o.kKm = dmul(kK, o.m);
   // k = kK r of A itself = kK m 2^(kr + e): for unscaled data (e = 0) the
   // exponent is added on the integer pipe (kK m 2^kr is a normal number:
   // J2+ >= 2^-1074 keeps r above 2^-537), otherwise by two exact scalings
@@ -885,7 +894,7 @@ __device__ __forceinline__ EigV eigvals_vjp_fwd(const Inv &v) {
   const double k =
       (v.e == 0) ? times_pow2(o.kKm, o.kr) : scale2k(scale2k(o.kKm, o.kr), v.e);
   o.e.r = o.m;  // r of the scaled data up to 2^kr (the fused kernel stores no r)
-  const double i3 = v.I1 * kInv3;
+  const double i3 = dmul(v.I1, kInv3);
   o.c12 = fma(2.0, o.e.sigma1, o.e.sigma2);
   o.e.l1 = fma(-k, o.c12, i3);
   o.e.l2 = fma(k, o.e.sigma1 - o.e.sigma2, i3);
@@ -907,10 +916,10 @@ __device__ __forceinline__ Adj adjoint_vjp(const EigV &f, double g1, double g2, 
   const double s3 = sigma1 + sigma2;
   const bool rz = hi_abs(f.m) < (1 << 20);  // r = 0: a triple eigenvalue
   const double km = rz ? kK : f.kKm;         // kK m, m = 1 for r = 0
-  const double s12 = s1 * s2;
-  const double P = s12 * s3;
+  const double s12 = dmul(s1, s2);
+  const double P = dmul(s12, s3);
   // Rh = (sqrt3/2) / (m P) = 1 / (3 kK m P): the factor in the seed (recip3_pos)
-  const double Rh = recip3_pos(km * P);
+  const double Rh = recip3_pos(dmul(km, P));
   double n12 = g2 - g1, n23 = g3 - g2;
   Adj o;
   // a_I1 = (g1 + g2 + g3)/3 = g2 + (n23 - n12)/3, finished in the gradient's
@@ -921,10 +930,10 @@ __device__ __forceinline__ Adj adjoint_vjp(const EigV &f, double g1, double g2, 
     n12 = z1 ? 0.0 : 0.5 * (g2 + g3) - g1;
     n23 = z2 ? 0.0 : g3 - 0.5 * (g1 + g2);
   }
-  const double s3Rh = s3 * Rh;
-  const double D23 = n23 * (s1 * s3Rh);
-  const double aJ3s = fma(-(n12 * s2), s3Rh, D23) * (s12 * Rh);
-  const double aJ2s = fma(-(f.kKm * f.c12), aJ3s, D23);
+  const double s3Rh = dmul(s3, Rh);
+  const double D23 = dmul(n23, dmul(s1, s3Rh));
+  const double aJ3s = dmul(fma(-dmul(n12, s2), s3Rh, D23), dmul(s12, Rh));
+  const double aJ2s = fma(-dmul(f.kKm, f.c12), aJ3s, D23);
   o.aJ2s = rz ? 0.0 : aJ2s;
   o.aJ3s = rz ? 0.0 : aJ3s;
   o.k = rz ? 0 : f.kr;
@@ -955,8 +964,8 @@ __device__ __forceinline__ int vjp_units(const Adj &s, int hmax, double &b2, dou
 // (as grad_general: a_I1 I + a_J2 dev(A)^T + a_J3 dev(cof dev A)).
 __device__ __forceinline__ void grad_general_vjp(const ShareG &x, double J2, const Adj &s,
                                                  double (&G)[9]) {
-  double D[9] = {x.tn * kInv3, x.a01, x.a02, x.a10, -(x.t2 * kInv3), x.a12, x.a20, x.a21,
-                 -(x.t1 * kInv3)};
+  double D[9] = {dmul(x.tn, kInv3), x.a01, x.a02, x.a10, -dmul(x.t2, kInv3), x.a12, x.a20, x.a21,
+                 -dmul(x.t1, kInv3)};
   int h = hi_abs(D[0]);
 #pragma unroll
   for (int j = 1; j < 9; ++j) h = max(h, hi_abs(D[j]));
@@ -981,12 +990,12 @@ __device__ __forceinline__ void grad_general_vjp(const ShareG &x, double J2, con
   // off-diagonal: b2 S_ji + b3 (P - S_ji S_kk) = S_ji (b2 - b3 S_kk) + b3 P, the
   // bracket shared by the two entries with the same S_kk
   const double q0 = fma(-b3, D[0], b2), q4 = fma(-b3, D[4], b2), q8 = fma(-b3, D[8], b2);
-  G[1] = fma(D[3], q8, b3 * P[1]);
-  G[3] = fma(D[1], q8, b3 * P[3]);
-  G[2] = fma(D[6], q4, b3 * P[2]);
-  G[6] = fma(D[2], q4, b3 * P[6]);
-  G[5] = fma(D[7], q0, b3 * P[5]);
-  G[7] = fma(D[5], q0, b3 * P[7]);
+  G[1] = fma(D[3], q8, dmul(b3, P[1]));
+  G[3] = fma(D[1], q8, dmul(b3, P[3]));
+  G[2] = fma(D[6], q4, dmul(b3, P[2]));
+  G[6] = fma(D[2], q4, dmul(b3, P[6]));
+  G[5] = fma(D[7], q0, dmul(b3, P[5]));
+  G[7] = fma(D[5], q0, dmul(b3, P[7]));
 }
 
 // The symmetric form (gradient with respect to the six stored entries, as

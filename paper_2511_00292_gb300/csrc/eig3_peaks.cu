@@ -14,17 +14,21 @@
 //              the DFMA are counted); 6 FFMA2 (the packed two-lane binary32
 //              FMA, __ffma2_rn: one instruction, two FMAs), 7 FFMA2 with one
 //              integer operation per FFMA2 (whether the packed form leaves
-//              issue slots free for other work; only the FFMA2 are counted)
+//              issue slots free for other work; only the FFMA2 are counted),
+//              8 binary64 multiplications on the integer pipes
+//              (softfp::mul_rn_int, the kernels' dmul)
 //     chains   independent chains per thread: 2, 4, 8 or 16
 //     blocks, threads   launch shape (threads <= 1024)
 //     iters    loop trips; every trip issues `chains` instructions of `kind`
 //              per thread
 //     out      device buffer of blocks * threads elements (double for kinds
-//              0-2, 4, 5, float for 3, 6, 7): each thread's result, so that
+//              0-2, 4, 5, 8, float for 3, 6, 7): each thread's result, so that
 //              nothing is optimised away
 //   Returns the cudaError_t of the launch (0 on success); asynchronous on
 //   `stream`.  Instructions executed = blocks * threads * iters * chains.
 #include <cuda_runtime.h>
+
+#include "eig3_dmul.cuh"
 
 namespace {
 
@@ -44,6 +48,7 @@ __global__ void __launch_bounds__(1024) k_peak64(int iters, double a, double b,
       if constexpr (KIND == 0) x[j] = fma(x[j], y[j], b);
       if constexpr (KIND == 1) x[j] = x[j] * y[j];
       if constexpr (KIND == 2) x[j] = x[j] + b;
+      if constexpr (KIND == 8) x[j] = eig3::softfp::mul_rn_int(x[j], y[j]);
     }
   }
   double s = 0.0;
@@ -149,6 +154,7 @@ int launch(int kind, int blocks, int threads, int iters, void *out, cudaStream_t
       k_peak32x2<0, C><<<blocks, threads, 0, s>>>(iters, (float)a, (float)b,
                                                   static_cast<float *>(out));
       break;
+    case 8: k_peak64<8, C><<<blocks, threads, 0, s>>>(iters, a, b, o64); break;
     case 7:
       k_peak32x2<1, C><<<blocks, threads, 0, s>>>(iters, (float)a, (float)b,
                                                   static_cast<float *>(out));

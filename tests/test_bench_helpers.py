@@ -157,6 +157,48 @@ def test_stored_counters_describe_the_committed_source(name):
     assert c["fp64_pipe_inst"] >= c["dfma"] + c["dmul"] + c["dadd"]
 
 
+# The functions on each kernel's path through eig3_f64.cuh that form binary64
+# products on the integer pipes (dmul), with the number of times the kernel
+# calls each per matrix.
+INT_DMUL_PATH = {
+    "vjp_f64_general9": {"invariants_general": 1, "dx13": 2, "triple_angle_sines": 1,
+                         "eigvals_vjp_fwd": 1, "adjoint_vjp": 1, "grad_general_vjp": 1},
+    "fwd_f64_general9": {"invariants_general": 1, "dx13": 2, "triple_angle_sines": 1,
+                         "eigvals_from_inv": 1},
+}
+
+
+@pytest.mark.parametrize("name", sorted(INT_DMUL_PATH))
+def test_integer_pipe_products_counted_from_the_source(name):
+    """The roofline counts each matrix's integer-pipe products (int_dmul) as
+    the dmul call sites on the kernel's path (straight-line code, one
+    execution each); every function reached from the path that forms such
+    products is on it."""
+    import re
+    text = _strip_comments(open(os.path.join(bench.ROOT, "paper_2511_00292_gb300", "csrc",
+                                             "eig3_f64.cuh")).read())
+    path = INT_DMUL_PATH[name]
+
+    def body(f):
+        d = bench._definitions(text, f)
+        assert len(d) == 1, (f, len(d))
+        return d[0]
+
+    defined = {m.group(1) for m in re.finditer(r"__device__[^;{]*?(\w+)\s*\(", text)}
+
+    def forms_dmul(f, seen=()):
+        b = body(f)
+        return "dmul(" in b or any(forms_dmul(g, seen + (f,)) for g in
+                                   set(re.findall(r"\b(\w+)\s*\(", b)) & defined
+                                   if g not in seen and g != f and g != "dmul")
+
+    total = sum(k * body(f).count("dmul(") for f, k in path.items())
+    assert total == bench.KERNEL_COUNTERS[name]["int_dmul"]
+    for f in path:
+        for g in set(re.findall(r"\b(\w+)\s*\(", body(f))) & defined - {"dmul", f}:
+            assert g in path or not forms_dmul(g), (f, g)
+
+
 def test_self_launch_command():
     """--gpus N outside torchrun re-runs the same command under
     torch.distributed.run: one rank per GPU, rendezvous on 127.0.0.1."""
