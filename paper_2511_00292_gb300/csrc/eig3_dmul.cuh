@@ -186,7 +186,10 @@ double mul_rn_slow(double x, double y) {
 
 // x * y rounded to nearest even (see the file comment).  The fast path takes
 // two normal operands whose product's exponent is in the normal range; all
-// else goes to mul_rn_slow.
+// else goes to mul_rn_slow.  The exponent stays a field word throughout:
+// ew = fa + fb - 1024 * 2^20 (+ 2^20 when P >= 2^127) is the result's biased
+// exponent minus one at bit 20, in range exactly when it is below 2046 * 2^20
+// as an unsigned number, and the significand's leading bit adds the last 1.
 EIG3_HD double mul_rn_int(double x, double y) {
   const uint64_t a = to_bits(x), b = to_bits(y);
   const uint32_t ahi = (uint32_t)(a >> 32), alo = (uint32_t)a;
@@ -195,19 +198,25 @@ EIG3_HD double mul_rn_int(double x, double y) {
   // significands << 11: (ah, al), (bh, bl) in [2^63, 2^64)
   const uint32_t ah = ((ahi | 0x100000u) << 11) | (alo >> 21), al = alo << 11;
   const uint32_t bh = ((bhi | 0x100000u) << 11) | (blo >> 21), bl = blo << 11;
-  uint32_t h, l;
-  bool low_nz;
-  mul_hi128(ah, al, bh, bl, h, l, low_nz);
-  const uint32_t top = h >> 31;
-  const uint32_t s = top ^ 1u;  // shift left by one when P < 2^127
-  const uint32_t hn = (h << s) | ((l >> 31) & s);
-  const uint32_t ln = (l << s) | (low_nz ? 1u : 0u);
-  // biased exponent of the result: ea + eb - 1023 + top
-  const int E = (int)((fa >> 20) + (fb >> 20) + top) - 1023;
+  const uint64_t t0 = (uint64_t)al * bl;
+  const uint64_t t1 = (uint64_t)ah * bl + (t0 >> 32);
+  const uint64_t t2 = (uint64_t)al * bh + (uint32_t)t1;
+  const uint64_t t3 = (uint64_t)ah * bh + (t1 >> 32) + (t2 >> 32);
+  const uint32_t h = (uint32_t)(t3 >> 32), l = (uint32_t)t3;
+  const bool top = (int32_t)h < 0;  // P >= 2^127
+  const uint32_t hn = top ? h : (h << 1) | (l >> 31);
+  const uint32_t ln = top ? l : l << 1;
+  const uint32_t ew = fa + fb + (top ? 0xc0100000u : 0xc0000000u);
   const bool fast = (fa - 0x100000u) < 0x7fe00000u && (fb - 0x100000u) < 0x7fe00000u &&
-                    (unsigned)(E - 1) < 2046u;
+                    ew < 0x7fe00000u;
   if (!fast) return mul_rn_slow(x, y);
-  return round_pack((ahi ^ bhi) & 0x80000000u, E, hn, ln);
+  // round at bit 11: up when the rounding bit (10) is set and a lower bit of
+  // P (the sticky bit) or the last kept bit (11) is
+  const bool sticky = ((ln & 0x3ffu) | (uint32_t)t2 | (uint32_t)t0) != 0;
+  const uint32_t up = (ln >> 10) & ((ln >> 11) | (sticky ? 1u : 0u)) & 1u;
+  const uint32_t lo = ((ln >> 11) | (hn << 21)) + up;
+  const uint32_t hi = ((ahi ^ bhi) & 0x80000000u) + ew + (hn >> 11) + (lo < up ? 1u : 0u);
+  return from_bits(hi, lo);
 }
 
 }  // namespace softfp
