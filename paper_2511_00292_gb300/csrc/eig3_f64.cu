@@ -11,7 +11,9 @@
 // 16-byte copies while the current tile is computed (eig3_tile.cuh).  The
 // adjoint inputs (16- or 32-byte rows) move with direct vector accesses and
 // the outputs are stored directly.  The binary64 path is bound by the FP64 pipe
-// (two DFMA per SM per clock on GB300, far below what HBM could feed).
+// (two DFMA per SM per clock on GB300, far below what HBM could feed) and, with
+// part of its products formed on the integer pipes (dmul), by the latency of
+// the two.
 #include <atomic>
 #include <cstdint>
 

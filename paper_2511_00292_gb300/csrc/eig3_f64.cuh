@@ -22,9 +22,10 @@
 namespace eig3 {
 
 // A binary64 product on the integer pipes (softfp::mul_rn_int: the same bits
-// as x * y).  The kernels are bound by the FP64 pipe while their integer
-// pipes are nearly idle, so the products of the invariants (Algorithms 2, 4
-// and 5) are formed here and the FP64 pipe keeps the FMAs and the rest.
+// as x * y).  With every operation on the FP64 pipe the kernels were bound by
+// it while their integer pipes sat nearly idle, so the plain products of the
+// invariants (Algorithms 2, 4 and 5), of the triple angle and of the adjoint
+// are formed here and the FP64 pipe keeps the FMAs, the additions and the rest.
 __device__ __forceinline__ double dmul(double x, double y) { return softfp::mul_rn_int(x, y); }
 
 // Constants (binary64 nearest values).
