@@ -1,6 +1,6 @@
 // Binary64 multiplication on the integer pipes.
 //
-// On this GPU the FP64 unit issues two lanes per SM per clock, a 64th of the
+// On GB300 the FP64 unit issues two lanes per SM per clock, a 64th of the
 // FP32 rate, while the integer units sit nearly idle in the binary64 kernels.
 // mul_rn_int computes the IEEE 754 binary64 product rounded to nearest, ties
 // to even, with 32-bit integer operations only: the same bits as the hardware
