@@ -11,8 +11,9 @@ L2 flush is needed between steps.
 
 Printed (rank 0, one JSON line): whole-job throughput in G matrices/s, the
 roofline of the dominant kernel (the fused binary64 kernel) and of the
-binary64 forward, both against FP64 / FP32 peaks measured in the same run by
-throughput loops, per-path throughputs of the other workloads' shapes (among
+binary64 forward, both against peaks measured in the same run by throughput
+loops (the FP64 pipe's DFMA rate plus the rate of the binary64 products the
+kernels form on the integer pipes; the FP32 rate beside them), per-path throughputs of the other workloads' shapes (among
 them the step as one CUDA graph of 10 steps, and unfused), the CPU oracle
 timed on the host cores on a bounded sample (with the max error over the
 stability bound of the GPU results on that sample, and the distance of the
@@ -21,7 +22,7 @@ per invariant), an end-to-end number through host buffers, and SM clocks
 sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --peaks            (the FP64 / FP32 pipe peaks alone)
+  python bench.py --peaks            (the FP64 / FP32 / integer-pipe product peaks alone)
   python bench.py --only KERNEL --n N (one kernel alone, for profiler captures)
 """
 from __future__ import annotations
