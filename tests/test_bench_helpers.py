@@ -223,3 +223,30 @@ def test_whole_job_throughput():
     v = bench.weak_scaling_value(8, 1 << 28, 62.8)
     assert v == pytest.approx(8 * (1 << 28) / 0.0628 / 1e9)
     assert bench.weak_scaling_value(1, 1 << 28, 62.8) == pytest.approx(v / 8)
+
+
+def test_kernel_roofline_counts_integer_pipe_products(monkeypatch):
+    """The roofline's flop count adds the integer-pipe products to the FP64
+    pipe's (FMA = 2), its peak is the two measured peaks added, and every
+    figure taken from the counters is null once they are stale."""
+    fp = {"fp64_tflops_measured": 1.0, "fp64_tinst_per_s": 0.5, "int_dmul_tops_measured": 0.5,
+          "fp32_tflops_measured": 78.0}
+    c = dict(bench.KERNEL_COUNTERS["vjp_f64_general9"])
+    c.update(dfma=100.0, dmul=10.0, dadd=30.0, int_dmul=60, fp64_warp_inst_x32=140.0,
+             fp64_pipe_inst=140.0, dram_bytes=200.0)
+    monkeypatch.setitem(bench.KERNEL_COUNTERS, "vjp_f64_general9", c)
+    monkeypatch.setattr(bench, "kernel_source_md5", lambda sources: c["source_md5"])
+    n, ms = 1 << 20, 1.0
+    r = bench.kernel_roofline("vjp_f64_general9", "k", n, ms, fp, 2000.0, 100, 7000.0)
+    flop = 2 * 100 + 10 + 30 + 60
+    assert r["algorithmic_per_matrix"]["flop"] == flop
+    assert r["peak"] == 1.5
+    assert abs(r["achieved"] - flop * n / 1e-3 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / 1.5) < 1e-12
+    assert abs(r["frac_vs_fp64_peak"] - r["achieved"] / 1.0) < 1e-12
+    assert abs(r["mix_ceiling"] - (2 * 100 + 10 + 30) / (2 * 140.0)) < 1e-12
+    assert r["traffic"] == 200.0 * n
+    monkeypatch.setattr(bench, "kernel_source_md5", lambda sources: "stale")
+    r = bench.kernel_roofline("vjp_f64_general9", "k", n, ms, fp, 2000.0, 100, 7000.0)
+    assert not r["counters_fresh"]
+    assert all(r[k] is None for k in ("achieved", "frac", "frac_vs_fp64_peak", "traffic"))
